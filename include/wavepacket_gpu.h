@@ -1,0 +1,185 @@
+/*
+ * wavepacket_gpu.h -- C ABI of the GB300 (sm_103a) split-operator propagator.
+ *
+ * The library advances a wave function psi(x, t) on a periodic 1-, 2- or 3-D grid
+ * under the time-dependent Schroedinger equation  i hbar dpsi/dt = (P^2/2m + V(x,t)) psi
+ * (Dion, Hashemloo, Rahali, arXiv:1306.3247, Sec. 2.1, eqs. (1)-(2)) with the
+ * symmetric split-operator step of eq. (splitop), the kinetic factor applied in
+ * momentum space through forward/inverse FFTs (eq. (ft)).
+ *
+ * Conventions used by every call:
+ *  - Grid (eq. (grid), Sec. 2.1): x_{d,i} = xmin[d] + i * L[d]/n[d], i = 0..n[d]-1,
+ *    periodic with period L[d]. A paper-style closed interval [x_min, x_max] with n
+ *    points maps to L = n (x_max - x_min)/(n - 1).
+ *  - Layout (Sec. 3.2.4): psi is row-major psi[n0][n1][n2], the last axis fastest.
+ *    1-D problems lie along x, 2-D problems in the xy plane (Sec. 2.2).
+ *  - Every n[d] is a power of two, 2 <= n[d]; other sizes return WP_EUNSUPPORTED.
+ *  - Momentum grid (Sec. 2.1): k_{d,j} = 2 pi j'/L[d], j' = j for j < n/2, j - n otherwise.
+ *  - Times: t_s = t0 + s dt for step index s (a product, never a running sum).
+ *  - Errors: every call returns a wp_status; nothing aborts (replaces abort() of
+ *    Sec. 3.2.6). wp_last_error() gives the handle's last message.
+ *  - Streams: all device work of a handle is ordered on the stream given at creation
+ *    (NULL = the legacy default stream). Calls that return host data synchronise it.
+ *  - Ownership: the library owns every buffer it allocates; caller buffers passed in
+ *    are only read or written during the call.
+ */
+#ifndef WAVEPACKET_GPU_H
+#define WAVEPACKET_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WP_OK = 0,
+  WP_EINVAL = 1,        /* bad argument (null pointer, nprint > nt as in Sec. 3.4, ...) */
+  WP_EUNSUPPORTED = 2,  /* size not a power of two, ndim outside 1..3, too large a line */
+  WP_ENOMEM = 3,        /* device allocation failed */
+  WP_ENONFINITE = 4,    /* the norm became NaN or infinite */
+  WP_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  WP_ECUDA = 6,         /* any other CUDA error; see wp_last_error */
+  WP_EBUSY = 7          /* the handle is in use (e.g. a batch slot is occupied) */
+} wp_status;
+
+/* Arithmetic form of the propagation.
+ *  WP_C128: complex128 state, FP64 FFT and phases (the plain FP64 method).
+ *  WP_C64:  complex64 state and FFT in FP32; twiddles, phase-argument reductions
+ *           modulo 2 pi and all observable reductions in FP64. */
+typedef enum { WP_C128 = 0, WP_C64 = 1 } wp_precision;
+
+/* Operator order of one step (eq. (splitop)).
+ *  WP_ORDER_VKV: e^{-iV(t_{s+1})dt/2hbar} e^{-iK dt/hbar} e^{-iV(t_s)dt/2hbar}
+ *                (trapezoid rule for the integral of V).
+ *  WP_ORDER_KVK: e^{-iK dt/2hbar} e^{-iV(t_s + dt/2)dt/hbar} e^{-iK dt/2hbar}
+ *                (the paper's order, mid-point rule, Algorithm 1).
+ * Adjacent half-steps of consecutive steps are merged on the device; the result
+ * differs from the unmerged product only by rounding. */
+typedef enum { WP_ORDER_VKV = 0, WP_ORDER_KVK = 1 } wp_order;
+
+/* Problem statement: the grid, mass and hbar, and the time step of Tab. 1
+ * (units = the value of hbar: 1 for atomic units, 1.054571726e-34 for SI). */
+typedef struct {
+  int32_t ndim;       /* 1, 2 or 3 */
+  int32_t precision;  /* wp_precision */
+  int32_t order;      /* wp_order */
+  int32_t autocorr;   /* nonzero: keep psi(t0) on the device for |<psi(0)|psi(t)>|^2 */
+  int64_t n[3];       /* grid points per axis; axes >= ndim are ignored */
+  double xmin[3];     /* first grid point per axis */
+  double L[3];        /* period per axis (dx = L/n) */
+  double mass, hbar, dt, t0;
+} wp_problem;
+
+/* Potential V(x,t) = sum over terms of f(t) * shape(x,t), evaluated on the device
+ * every step. It plays the role of the user potential() of Sec. 3.2.3.
+ * shape (centre c_d(t) = c0[d] + v[d] t):
+ *   WP_SHAPE_CONST   1
+ *   WP_SHAPE_QUAD    0.5 * sum_d a[d] (x_d - c_d)^2
+ *   WP_SHAPE_LINEAR  sum_d a[d] (x_d - c_d)
+ *   WP_SHAPE_GAUSS   exp(-sum_{d: a[d] > 0} (x_d - c_d)^2 / a[d]^2)
+ *   WP_SHAPE_MORSE   a[0] (1 - exp(-a[1] (x_k - c_k)))^2 along axis k = (int)a[2]
+ * time coefficient: f(t) = A0 + A env(t) sin(omega t + phi), with
+ *   WP_ENV_NONE   env = 1
+ *   WP_ENV_GAUSS  env = exp(-(t - t0)^2 / tau^2)
+ *   WP_ENV_SIN2   env = sin^2(pi t / tau) for t0 <= t <= t0 + tau, else 0 (Sec. 4.1)
+ * At most WP_MAX_TERMS terms, of which at most WP_MAX_GAUSS Gaussian shapes. */
+enum { WP_SHAPE_CONST = 0, WP_SHAPE_QUAD = 1, WP_SHAPE_LINEAR = 2, WP_SHAPE_GAUSS = 3, WP_SHAPE_MORSE = 4 };
+enum { WP_ENV_NONE = 0, WP_ENV_GAUSS = 1, WP_ENV_SIN2 = 2 };
+#define WP_MAX_TERMS 8
+#define WP_MAX_GAUSS 2
+
+typedef struct {
+  int32_t shape, env;
+  double a[3], c0[3], v[3];
+  double A0, A, omega, phi, t0, tau;
+} wp_pot_term;
+
+typedef struct {
+  int32_t nterms;
+  int32_t reserved;
+  wp_pot_term term[WP_MAX_TERMS];
+} wp_potential;
+
+/* Observables of Tab. 3 at one time (Sec. 3.4: at t0 and every nprint steps).
+ * Expectation values are the plain integrals <psi|A|psi> (not divided by the
+ * norm squared): x[d] = <x_d>, x2[d] = <x_d^2> (so the width of Tab. 3 is
+ * x2 - x^2), p[d] = <p_d>, energy = ekin + epot = <psi|H|psi>.
+ * autocorr = |<psi(t0)|psi(t)>|^2 when enabled, else 0. */
+typedef struct {
+  double t, norm;
+  double x[3], p[3], x2[3];
+  double energy, ekin, epot, autocorr;
+  int64_t step;
+} wp_obs;
+
+typedef struct wp_handle wp_handle;
+
+/* Create a propagator for one problem (Sec. 3.2.1 parameters). Allocates the state,
+ * one state-sized scratch buffer for the momentum-space observables, and small tables.
+ * stream: a cudaStream_t or NULL. On success *out owns the handle. */
+wp_status wp_create(const wp_problem* problem, void* stream, wp_handle** out);
+
+/* Set the potential (Sec. 3.2.2-3.2.3). Copied; may be called again between steps. */
+wp_status wp_set_potential(wp_handle* h, const wp_potential* pot);
+
+/* Copy a complex128 row-major psi into the state (Sec. 3.2.4 initialize_wf).
+ * on_device = 0: psi is host memory; 1: device memory. The step index is kept. */
+wp_status wp_set_state(wp_handle* h, const void* psi, int on_device);
+
+/* Fill the state with the normalised Gaussian packet of Sec. 4.2:
+ * (2/pi)^{d/4} prod_d sigma_d^{-1/2} e^{i p0_d (x_d - x0_d)/hbar} e^{-(x_d - x0_d)^2/sigma_d^2}. */
+wp_status wp_init_gaussian(wp_handle* h, const double x0[3], const double p0[3], const double sigma[3]);
+
+/* Copy the state out as complex128 row-major (on_device as in wp_set_state). */
+wp_status wp_get_state(wp_handle* h, void* dst, int on_device);
+
+/* Advance nsteps >= 0 split-operator steps (eq. (splitop), Algorithm 1 inner loop).
+ * Asynchronous on the handle's stream. */
+wp_status wp_step(wp_handle* h, int64_t nsteps);
+
+/* Evaluate the observables of Tab. 3 at the current step (synchronises). */
+wp_status wp_observe(wp_handle* h, wp_obs* out);
+
+/* Algorithm 1: observables at the current step and after every nprint steps,
+ * nt steps in all (all nt run even when nprint does not divide nt, Sec. 3.4).
+ * obs: caller-owned host array of at least 1 + nt/nprint records; *nobs gets the count.
+ * nprint > nt or nprint <= 0 -> WP_EINVAL. A NaN/Inf norm -> WP_ENONFINITE. */
+wp_status wp_run(wp_handle* h, int64_t nt, int64_t nprint, wp_obs* obs, int64_t* nobs);
+
+/* Unnormalised in-place FFT of the state over all axes (eq. (ft)); sign -1 forward,
+ * +1 inverse. The step index is unchanged. */
+wp_status wp_fft(wp_handle* h, int sign);
+
+/* Borrowed device pointer to the state, valid until wp_destroy. Element type is
+ * complex128 (WP_C128) or complex64 (WP_C64), row-major. */
+void* wp_state_ptr(wp_handle* h);
+
+/* Current step index s (t_s = t0 + s dt); settable for checkpoint/resume. */
+int64_t wp_get_step_index(const wp_handle* h);
+wp_status wp_set_step_index(wp_handle* h, int64_t s);
+
+/* Kernel timing for measurement: while enabled, every launch is bracketed by CUDA
+ * events on the handle's stream (CUDA-graph replay is off). wp_profile_read returns
+ * the launch count and total milliseconds recorded for one kernel class (names as in
+ * wp_kernel_name; index < wp_kernel_count()) and clears it. */
+wp_status wp_profile_enable(wp_handle* h, int enable);
+wp_status wp_profile_read(wp_handle* h, int kernel, int64_t* launches, double* total_ms);
+int wp_kernel_count(void);
+const char* wp_kernel_name(int kernel);
+
+/* Launches of the library's kernels issued by this handle since creation. */
+int64_t wp_launch_count(const wp_handle* h);
+
+/* Release everything the handle owns. NULL is accepted. */
+wp_status wp_destroy(wp_handle* h);
+
+/* The handle's last error message ("" if none); a static string for NULL. */
+const char* wp_last_error(const wp_handle* h);
+const char* wp_status_string(wp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WAVEPACKET_GPU_H */

@@ -1,0 +1,915 @@
+// C ABI of the split-operator propagator (include/wavepacket_gpu.h): handle, plans,
+// tables and the step sequencer. All device work is issued on the handle's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "wp_internal.h"
+
+using namespace wp;
+
+namespace {
+
+constexpr int kTileLog = 11;  // target tile: 2048 elements (8 per thread, 256 threads)
+
+struct PassPlan {
+  int axis = 0;
+  int logn = 0, logC = 0, LS = 1, log_inner = 0, nthreads = 32, ept = 8;
+  int64_t ntiles = 0;
+  size_t smem = 0;
+};
+
+struct EventPair {
+  cudaEvent_t a, b;
+  int cls;
+};
+
+const char* kClassNames[K_NCLASSES] = {"pass_contig", "pass_strided", "pass_kinetic", "prep_tables",
+                                       "step1d_resident", "reduce_observables", "aux"};
+
+int ilog2(int64_t v) {
+  int l = 0;
+  while ((int64_t(1) << l) < v) l++;
+  return l;
+}
+
+bool is_pow2(int64_t v) { return v >= 1 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct wp_handle {
+  wp_problem pb{};
+  cudaStream_t stream = nullptr;
+  Geom g{};
+  int ndim = 1;
+  int64_t n[3] = {1, 1, 1};
+  int64_t N = 1;
+  size_t elem = 16;
+  bool f64 = true;
+  void* state = nullptr;
+  void* scratch = nullptr;
+  void* psi0 = nullptr;
+  void* staging = nullptr;  // complex128 staging for conversions (complex64 form)
+  Ctrl* ctrl = nullptr;
+  DevPot* dpot = nullptr;
+  DevPot hpot{};
+  void* tabmem = nullptr;
+  AxisTab<double> tab64[3]{};
+  AxisTab<float> tab32[3]{};
+  double* part_pos = nullptr;
+  double* part_mom = nullptr;
+  double* obs_dev = nullptr;
+  int64_t obs_cap = 0;
+  PassPlan plan[3];
+  int res_nthreads = 32;
+  int res_ept = 8;
+  size_t res_smem = 0;
+  int64_t host_step = 0;
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<EventPair> pending;
+  std::vector<cudaEvent_t> free_events;
+  double prof_ms[K_NCLASSES] = {};
+  int64_t prof_n[K_NCLASSES] = {};
+  std::string err;
+};
+
+namespace {
+
+std::string g_err;  // message for failures before a handle exists
+
+wp_status fail(wp_handle* h, wp_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_err = msg;
+  return st;
+}
+
+wp_status cuda_fail(wp_handle* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(h, e == cudaErrorMemoryAllocation ? WP_ENOMEM : WP_ECUDA, m);
+}
+
+#define WP_CUDA(h, call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+cudaEvent_t get_event(wp_handle* h) {
+  if (!h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Bracket one launch with events (when profiling) and count it.
+struct LaunchScope {
+  wp_handle* h;
+  int cls;
+  cudaEvent_t b = nullptr;
+  LaunchScope(wp_handle* hh, int c) : h(hh), cls(c) {
+    if (h->profiling) {
+      b = get_event(h);
+      cudaEventRecord(b, h->stream);
+    }
+  }
+  ~LaunchScope() {
+    h->launches++;
+    if (h->profiling) {
+      cudaEvent_t a = get_event(h);
+      cudaEventRecord(a, h->stream);
+      h->pending.push_back({b, a, cls});
+    }
+  }
+};
+
+wp_status launch_rc(wp_handle* h, int rc, const char* what) {
+  if (rc != 0) return cuda_fail(h, (cudaError_t)rc, what);
+  return WP_OK;
+}
+
+PassPlan make_plan(const wp_handle* h, int axis) {
+  PassPlan p;
+  p.axis = axis;
+  const int nd = h->ndim;
+  p.logn = h->g.ln[axis];
+  int log_inner = 0, log_outer = 0;
+  for (int d = axis + 1; d < nd; d++) log_inner += h->g.ln[d];
+  for (int d = 0; d < axis; d++) log_outer += h->g.ln[d];
+  p.log_inner = log_inner;
+  const bool contig = (axis == nd - 1);
+  const int lines_log = contig ? log_outer : log_inner;
+  int logC = kTileLog - p.logn;
+  if (logC < 0) logC = 0;
+  if (logC > 6) logC = 6;
+  if (logC > lines_log) logC = lines_log;
+  p.logC = logC;
+  const int C = 1 << logC;
+  p.LS = contig ? (C > 1 ? C + 1 : 1) : C;
+  const int64_t tile = int64_t(C) << p.logn;
+  const int E = tile <= 2048 ? 8 : 16;
+  int64_t thr = tile / E;
+  if (thr < 1) thr = 1;
+  p.ept = E;
+  p.nthreads = (int)((thr + 31) / 32 * 32);
+  p.ntiles = h->N / tile;
+  p.smem = (size_t)p.LS * ((size_t)1 << p.logn) * h->elem;
+  return p;
+}
+
+// Host-side tables in extended precision: twiddles exp(-2 pi i k/n) and the kinetic
+// factors exp(-i hbar k^2 tau/2m), argument reduced modulo 2 pi before cos/sin.
+void host_twiddles(int64_t n, std::vector<double>& re, std::vector<double>& im) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  re.resize(n);
+  im.resize(n);
+  for (int64_t k = 0; k < n; k++) {
+    const long double a = -2.0L * pi * (long double)k / (long double)n;
+    re[k] = (double)cosl(a);
+    im[k] = (double)sinl(a);
+  }
+}
+
+void host_kinetic(const wp_handle* h, int d, double tau, double scale, std::vector<double>& re,
+                  std::vector<double>& im) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  const int64_t n = h->n[d];
+  re.resize(n);
+  im.resize(n);
+  const long double L = h->pb.L[d];
+  for (int64_t j = 0; j < n; j++) {
+    const int64_t js = j < n / 2 ? j : j - n;
+    const long double k = 2.0L * pi * (long double)js / L;
+    long double th = -(long double)h->pb.hbar * k * k * (long double)tau / (2.0L * (long double)h->pb.mass);
+    th = fmodl(th, 2.0L * pi);
+    re[j] = (double)(cosl(th) * (long double)scale);
+    im[j] = (double)(sinl(th) * (long double)scale);
+  }
+}
+
+template <class T>
+AxisTab<T>* tabs(wp_handle* h);
+template <>
+AxisTab<double>* tabs<double>(wp_handle* h) {
+  return h->tab64;
+}
+template <>
+AxisTab<float>* tabs<float>(wp_handle* h) {
+  return h->tab32;
+}
+
+template <class T>
+wp_status alloc_tables(wp_handle* h) {
+  // per axis: W, Kfull, Khalf, P (complex T); G[g] (T); A, Gd[g] (double)
+  size_t bytes = 0;
+  auto add = [&](size_t b) {
+    size_t o = bytes;
+    bytes += (b + 255) / 256 * 256;
+    return o;
+  };
+  size_t off[3][4 + 2 * WP_MAX_GAUSS + 1];
+  size_t off_lo[3][4];
+  for (int d = 0; d < h->ndim; d++) {
+    const size_t n = (size_t)h->n[d];
+    for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
+    for (int k = 0; k < 4; k++) off_lo[d][k] = add(n * sizeof(cx<T>));
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][4 + gg] = add(n * sizeof(T));
+    off[d][4 + WP_MAX_GAUSS] = add(n * sizeof(double));
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][5 + WP_MAX_GAUSS + gg] = add(n * sizeof(double));
+  }
+  WP_CUDA(h, cudaMalloc(&h->tabmem, bytes));
+  WP_CUDA(h, cudaMemsetAsync(h->tabmem, 0, bytes, h->stream));
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  char* base = (char*)h->tabmem;
+  AxisTab<T>* tb = tabs<T>(h);
+  for (int d = 0; d < h->ndim; d++) {
+    tb[d].W = (cx<T>*)(base + off[d][0]);
+    tb[d].Kfull = (cx<T>*)(base + off[d][1]);
+    tb[d].Khalf = (cx<T>*)(base + off[d][2]);
+    tb[d].P = (cx<T>*)(base + off[d][3]);
+    tb[d].Kfull_lo = (cx<T>*)(base + off_lo[d][0]);
+    tb[d].Khalf_lo = (cx<T>*)(base + off_lo[d][1]);
+    tb[d].P_lo = (cx<T>*)(base + off_lo[d][2]);
+    tb[d].W_lo = (cx<T>*)(base + off_lo[d][3]);
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].G[gg] = (T*)(base + off[d][4 + gg]);
+    tb[d].A = (double*)(base + off[d][4 + WP_MAX_GAUSS]);
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].Gd[gg] = (double*)(base + off[d][5 + WP_MAX_GAUSS + gg]);
+  }
+  // static tables (high and low parts)
+  for (int d = 0; d < h->ndim; d++) {
+    std::vector<double> re, im;
+    const size_t n = (size_t)h->n[d];
+    std::vector<cx<T>> hi(n), lo(n);
+    auto split = [&]() {
+      for (size_t k = 0; k < n; k++) {
+        const T hr = (T)re[k], hm = (T)im[k];
+        hi[k] = cx<T>{hr, hm};
+        lo[k] = cx<T>{(T)(re[k] - (double)hr), (T)(im[k] - (double)hm)};
+      }
+    };
+    const size_t nb = n * sizeof(cx<T>);
+    host_twiddles(h->n[d], re, im);
+    split();
+    WP_CUDA(h, cudaMemcpy(tb[d].W, hi.data(), nb, cudaMemcpyHostToDevice));
+    WP_CUDA(h, cudaMemcpy(tb[d].W_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    const double scale = d == 0 ? 1.0 / (double)h->N : 1.0;
+    host_kinetic(h, d, h->pb.dt, scale, re, im);
+    split();
+    WP_CUDA(h, cudaMemcpy(tb[d].Kfull, hi.data(), nb, cudaMemcpyHostToDevice));
+    WP_CUDA(h, cudaMemcpy(tb[d].Kfull_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    host_kinetic(h, d, 0.5 * h->pb.dt, scale, re, im);
+    split();
+    WP_CUDA(h, cudaMemcpy(tb[d].Khalf, hi.data(), nb, cudaMemcpyHostToDevice));
+    WP_CUDA(h, cudaMemcpy(tb[d].Khalf_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+  }
+  return WP_OK;
+}
+
+// ------------------------------------------------------------------ launches
+template <class T>
+PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void* out, double* partials,
+                          int khalf) {
+  PassParams<T> p{};
+  const PassPlan& pl = h->plan[axis];
+  AxisTab<T>* tb = tabs<T>(h);
+  p.in = (cx<T>*)in;
+  p.out = (cx<T>*)out;
+  p.psi0 = (const cx<T>*)h->psi0;
+  p.g = h->g;
+  p.axis = axis;
+  p.logn = pl.logn;
+  p.logC = pl.logC;
+  p.LS = pl.LS;
+  p.log_inner = pl.log_inner;
+  p.nthreads = pl.nthreads;
+  p.ept = pl.ept;
+  p.flags = flags;
+  p.ngauss = h->hpot.ngauss;
+  p.khalf = khalf;
+  p.W = tb[axis].W;
+  p.W_lo = tb[axis].W_lo;
+  for (int d = 0; d < h->ndim; d++) {
+    p.K[d] = khalf ? tb[d].Khalf : tb[d].Kfull;
+    p.K_lo[d] = khalf ? tb[d].Khalf_lo : tb[d].Kfull_lo;
+    p.P[d] = tb[d].P;
+    p.P_lo[d] = tb[d].P_lo;
+    p.A[d] = tb[d].A;
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) {
+      p.G[gg][d] = tb[d].G[gg];
+      p.Gd[gg][d] = tb[d].Gd[gg];
+    }
+  }
+  p.ctrl = h->ctrl;
+  p.partials = partials;
+  return p;
+}
+
+template <class T>
+wp_status run_pass(wp_handle* h, int axis, uint32_t flags, void* in, void* out, double* partials = nullptr,
+                   int khalf = 0) {
+  const PassParams<T> p = pass_params<T>(h, axis, flags, in, out, partials, khalf);
+  int cls = (axis == h->ndim - 1) ? K_PASS_CONTIG : (flags & F_KIN) ? K_PASS_KIN : K_PASS_STRIDED;
+  if (axis == 0 && (flags & F_OBS_MOM)) cls = K_PASS_STRIDED;
+  LaunchScope ls(h, cls);
+  return launch_rc(h, launch_pass<T>(p, h->plan[axis].ntiles, h->plan[axis].smem, h->stream), "pass kernel");
+}
+
+template <class T>
+wp_status run_prep(wp_handle* h, int step_add, double t_shift, double tau) {
+  PrepParams<T> p{};
+  p.g = h->g;
+  for (int d = 0; d < 3; d++) p.n[d] = h->n[d];
+  AxisTab<T>* tb = tabs<T>(h);
+  for (int d = 0; d < h->ndim; d++) p.tab[d] = tb[d];
+  p.pot = h->dpot;
+  p.ctrl = h->ctrl;
+  p.step_add = step_add;
+  p.t_shift = t_shift;
+  p.tau = tau;
+  LaunchScope ls(h, K_PREP);
+  return launch_rc(h, launch_prep<T>(p, h->stream), "prep kernel");
+}
+
+wp_status run_set_step(wp_handle* h, int64_t step) {
+  LaunchScope ls(h, K_AUX);
+  return launch_rc(h, launch_set_step(h->ctrl, step, h->stream), "set-step kernel");
+}
+
+wp_status ensure_obs(wp_handle* h, int64_t cap) {
+  if (cap <= h->obs_cap) return WP_OK;
+  if (h->obs_dev) cudaFree(h->obs_dev);
+  h->obs_dev = nullptr;
+  h->obs_cap = 0;
+  WP_CUDA(h, cudaMalloc(&h->obs_dev, (size_t)cap * 16 * sizeof(double)));
+  h->obs_cap = cap;
+  return WP_OK;
+}
+
+template <class T>
+wp_status run_res1d(wp_handle* h, int64_t nsteps, bool obs) {
+  Res1dParams<T> p{};
+  AxisTab<T>* tb = tabs<T>(h);
+  p.psi = (cx<T>*)h->state;
+  p.psi0 = (const cx<T>*)h->psi0;
+  p.g = h->g;
+  p.logn = h->g.ln[0];
+  p.nthreads = h->res_nthreads;
+  p.ept = h->res_ept;
+  p.order = h->pb.order;
+  p.obs = obs ? 1 : 0;
+  p.autocorr = h->pb.autocorr ? 1 : 0;
+  p.nsteps = nsteps;
+  p.W = tb[0].W;
+  p.W_lo = tb[0].W_lo;
+  p.Kfull = tb[0].Kfull;
+  p.Khalf = tb[0].Khalf;
+  p.Kfull_lo = tb[0].Kfull_lo;
+  p.Khalf_lo = tb[0].Khalf_lo;
+  p.pot = h->dpot;
+  p.ctrl = h->ctrl;
+  p.obs_out = h->obs_dev;
+  p.obs_cap = h->obs_cap;
+  LaunchScope ls(h, K_RES1D);
+  return launch_rc(h, launch_res1d<T>(p, h->res_smem, h->stream), "1-D resident kernel");
+}
+
+// Observables of the clean (position-space) state at the device step index.
+template <class T>
+wp_status observe_seq(wp_handle* h, bool tables_ready) {
+  wp_status st;
+  const int nd = h->ndim;
+  if (nd == 1) return run_res1d<T>(h, 0, true);
+  if (!tables_ready)
+    if ((st = run_prep<T>(h, 0, 0.0, 0.0)) != WP_OK) return st;
+  const uint32_t ac = h->pb.autocorr ? F_AUTOCORR : 0u;
+  if ((st = run_pass<T>(h, nd - 1, F_OBS_POS | F_NO_STORE | ac, h->state, h->state, h->part_pos)) != WP_OK) return st;
+  return WP_OK;
+}
+
+// Momentum sums of the clean state through the scratch buffer, then the record.
+template <class T>
+wp_status momentum_and_reduce(wp_handle* h) {
+  wp_status st;
+  const int nd = h->ndim;
+  if ((st = run_pass<T>(h, nd - 1, F_FFT, h->state, h->scratch)) != WP_OK) return st;
+  if (nd == 3)
+    if ((st = run_pass<T>(h, 1, F_FFT, h->scratch, h->scratch)) != WP_OK) return st;
+  if ((st = run_pass<T>(h, 0, F_FFT | F_OBS_MOM | F_NO_STORE, h->scratch, h->scratch, h->part_mom)) != WP_OK)
+    return st;
+  ReduceParams r{};
+  r.pos = h->part_pos;
+  r.npos = h->plan[nd - 1].ntiles;
+  r.mom = h->part_mom;
+  r.nmom = h->plan[0].ntiles;
+  r.g = h->g;
+  r.ntotal = h->N;
+  r.autocorr = h->pb.autocorr ? 1 : 0;
+  r.ctrl = h->ctrl;
+  r.obs_out = h->obs_dev;
+  r.obs_cap = h->obs_cap;
+  LaunchScope ls(h, K_REDUCE);
+  return launch_rc(h, launch_reduce(r, h->stream), "reduce kernel");
+}
+
+// m >= 1 steps from a clean state; ends clean. obs_end: record observables at the end.
+template <class T>
+wp_status chunk_seq(wp_handle* h, int64_t m, bool obs_end) {
+  wp_status st;
+  const int nd = h->ndim;
+  const double dt = h->pb.dt;
+  if (nd == 1) {
+    st = run_res1d<T>(h, m, obs_end);
+    if (st == WP_OK) h->host_step += m;
+    return st;
+  }
+  void* S = h->state;
+  const int Z = nd - 1;
+  auto middle = [&](int khalf) -> wp_status {
+    wp_status s2;
+    if (nd == 3)
+      if ((s2 = run_pass<T>(h, 1, F_FFT, S, S)) != WP_OK) return s2;
+    if ((s2 = run_pass<T>(h, 0, F_KIN, S, S, nullptr, khalf)) != WP_OK) return s2;
+    if (nd == 3)
+      if ((s2 = run_pass<T>(h, 1, F_IFFT, S, S)) != WP_OK) return s2;
+    return WP_OK;
+  };
+  const uint32_t obsf = obs_end ? (F_OBS_POS | (h->pb.autocorr ? F_AUTOCORR : 0u)) : 0u;
+  if (h->pb.order == WP_ORDER_VKV) {
+    if ((st = run_prep<T>(h, 0, 0.0, 0.5 * dt)) != WP_OK) return st;
+    if ((st = run_pass<T>(h, Z, F_PHASE | F_FFT, S, S)) != WP_OK) return st;
+    if ((st = middle(0)) != WP_OK) return st;
+    for (int64_t k = 1; k < m; k++) {
+      if ((st = run_prep<T>(h, 1, 0.0, dt)) != WP_OK) return st;
+      if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
+      if ((st = middle(0)) != WP_OK) return st;
+    }
+    if ((st = run_prep<T>(h, 1, 0.0, 0.5 * dt)) != WP_OK) return st;
+    if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | obsf, S, S, h->part_pos)) != WP_OK) return st;
+  } else {
+    if ((st = run_pass<T>(h, Z, F_FFT, S, S)) != WP_OK) return st;
+    if ((st = middle(1)) != WP_OK) return st;
+    for (int64_t k = 0; k < m; k++) {
+      if ((st = run_prep<T>(h, k == 0 ? 0 : 1, 0.5 * dt, dt)) != WP_OK) return st;
+      if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
+      if ((st = middle(k == m - 1 ? 1 : 0)) != WP_OK) return st;
+    }
+    if ((st = run_prep<T>(h, 1, 0.0, 0.0)) != WP_OK) return st;
+    if ((st = run_pass<T>(h, Z, F_IFFT | obsf, S, S, h->part_pos)) != WP_OK) return st;
+  }
+  h->host_step += m;
+  if (obs_end) return momentum_and_reduce<T>(h);
+  return WP_OK;
+}
+
+template <class T>
+wp_status fft_seq(wp_handle* h, int sign) {
+  wp_status st;
+  if (h->ndim == 1) {
+    // a 1-D line is a contiguous pass with a single tile of one line
+    PassPlan save = h->plan[0];
+    PassPlan pl = save;
+    pl.logC = 0;
+    pl.LS = 1;
+    pl.log_inner = 0;
+    pl.ntiles = 1;
+    pl.ept = (int64_t(1) << pl.logn) <= 2048 ? 8 : 16;
+    const int64_t thr = std::max<int64_t>(1, (int64_t(1) << pl.logn) / pl.ept);
+    pl.nthreads = (int)((thr + 31) / 32 * 32);
+    pl.smem = ((size_t)1 << pl.logn) * h->elem;
+    h->plan[0] = pl;
+    st = run_pass<T>(h, 0, sign < 0 ? F_FFT : F_IFFT, h->state, h->state);
+    h->plan[0] = save;
+    return st;
+  }
+  for (int d = h->ndim - 1; d >= 0; d--)
+    if ((st = run_pass<T>(h, d, sign < 0 ? F_FFT : F_IFFT, h->state, h->state)) != WP_OK) return st;
+  return WP_OK;
+}
+
+wp_status check_device_error(wp_handle* h) {
+  Ctrl c{};
+  WP_CUDA(h, cudaMemcpyAsync(&c, h->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (c.err == WP_ENONFINITE) return fail(h, WP_ENONFINITE, "norm is not finite");
+  if (c.err != 0) return fail(h, (wp_status)c.err, "device error");
+  return WP_OK;
+}
+
+template <class T>
+wp_status run_impl(wp_handle* h, int64_t nt, int64_t nprint, wp_obs* obs, int64_t* nobs) {
+  wp_status st;
+  const int64_t nrec = 1 + nt / nprint;
+  if ((st = ensure_obs(h, nrec)) != WP_OK) return st;
+  if ((st = run_set_step(h, h->host_step)) != WP_OK) return st;
+  if ((st = observe_seq<T>(h, false)) != WP_OK) return st;
+  if (h->ndim > 1)
+    if ((st = momentum_and_reduce<T>(h)) != WP_OK) return st;
+  for (int64_t c = 0; c < nt / nprint; c++)
+    if ((st = chunk_seq<T>(h, nprint, true)) != WP_OK) return st;
+  if (nt % nprint)
+    if ((st = chunk_seq<T>(h, nt % nprint, false)) != WP_OK) return st;
+  std::vector<double> buf((size_t)nrec * 16);
+  WP_CUDA(h, cudaMemcpyAsync(buf.data(), h->obs_dev, buf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                             h->stream));
+  if ((st = check_device_error(h)) != WP_OK) return st;
+  for (int64_t r = 0; r < nrec; r++) {
+    const double* q = &buf[r * 16];
+    wp_obs& o = obs[r];
+    o.t = q[0];
+    o.norm = q[1];
+    for (int d = 0; d < 3; d++) {
+      o.x[d] = q[2 + d];
+      o.p[d] = q[5 + d];
+      o.x2[d] = q[8 + d];
+    }
+    o.energy = q[11];
+    o.ekin = q[12];
+    o.epot = q[13];
+    o.autocorr = q[14];
+    o.step = (int64_t)q[15];
+  }
+  if (nobs) *nobs = nrec;
+  return WP_OK;
+}
+
+template <class T>
+wp_status observe_impl(wp_handle* h, wp_obs* out) {
+  wp_obs tmp[1];
+  wp_status st;
+  if ((st = ensure_obs(h, 1)) != WP_OK) return st;
+  if ((st = run_set_step(h, h->host_step)) != WP_OK) return st;
+  if ((st = observe_seq<T>(h, false)) != WP_OK) return st;
+  if (h->ndim > 1)
+    if ((st = momentum_and_reduce<T>(h)) != WP_OK) return st;
+  double q[16];
+  WP_CUDA(h, cudaMemcpyAsync(q, h->obs_dev, sizeof(q), cudaMemcpyDeviceToHost, h->stream));
+  if ((st = check_device_error(h)) != WP_OK) return st;
+  wp_obs& o = tmp[0];
+  o.t = q[0];
+  o.norm = q[1];
+  for (int d = 0; d < 3; d++) {
+    o.x[d] = q[2 + d];
+    o.p[d] = q[5 + d];
+    o.x2[d] = q[8 + d];
+  }
+  o.energy = q[11];
+  o.ekin = q[12];
+  o.epot = q[13];
+  o.autocorr = q[14];
+  o.step = (int64_t)q[15];
+  *out = o;
+  return WP_OK;
+}
+
+template <class T>
+wp_status convert_in(wp_handle* h, const void* src_dev) {
+  ConvParams<T> p{};
+  p.src = src_dev;
+  p.dst = h->state;
+  p.n = h->N;
+  p.dir = 0;
+  LaunchScope ls(h, K_AUX);
+  return launch_rc(h, launch_convert<T>(p, h->stream), "convert kernel");
+}
+
+template <class T>
+wp_status convert_out(wp_handle* h, void* dst_dev) {
+  ConvParams<T> p{};
+  p.src = h->state;
+  p.dst = dst_dev;
+  p.n = h->N;
+  p.dir = 1;
+  LaunchScope ls(h, K_AUX);
+  return launch_rc(h, launch_convert<T>(p, h->stream), "convert kernel");
+}
+
+wp_status save_psi0(wp_handle* h) {
+  if (!h->pb.autocorr) return WP_OK;
+  WP_CUDA(h, cudaMemcpyAsync(h->psi0, h->state, (size_t)h->N * h->elem, cudaMemcpyDeviceToDevice, h->stream));
+  return WP_OK;
+}
+
+template <class T>
+wp_status gaussian_impl(wp_handle* h, const double* x0, const double* p0, const double* sigma) {
+  GaussParams<T> p{};
+  p.psi = (cx<T>*)h->state;
+  p.g = h->g;
+  double pref = pow(2.0 / 3.14159265358979323846, 0.25 * h->ndim);
+  for (int d = 0; d < 3; d++) {
+    p.x0[d] = d < h->ndim ? x0[d] : 0.0;
+    p.p0[d] = d < h->ndim ? p0[d] : 0.0;
+    p.sigma[d] = d < h->ndim ? sigma[d] : 1.0;
+    if (d < h->ndim) pref /= sqrt(sigma[d]);
+  }
+  p.pref = pref;
+  {
+    LaunchScope ls(h, K_AUX);
+    wp_status st = launch_rc(h, launch_gaussian<T>(p, h->N, h->stream), "gaussian kernel");
+    if (st != WP_OK) return st;
+  }
+  return save_psi0(h);
+}
+
+wp_status validate_problem(const wp_problem* pb) {
+  if (!pb) return fail(nullptr, WP_EINVAL, "problem is NULL");
+  if (pb->ndim < 1 || pb->ndim > 3) return fail(nullptr, WP_EUNSUPPORTED, "ndim must be 1, 2 or 3");
+  if (pb->precision != WP_C128 && pb->precision != WP_C64) return fail(nullptr, WP_EINVAL, "unknown precision");
+  if (pb->order != WP_ORDER_VKV && pb->order != WP_ORDER_KVK) return fail(nullptr, WP_EINVAL, "unknown order");
+  for (int d = 0; d < pb->ndim; d++) {
+    if (!is_pow2(pb->n[d]) || pb->n[d] < 2)
+      return fail(nullptr, WP_EUNSUPPORTED, "every n[d] must be a power of two >= 2");
+    if (pb->n[d] > 8192) return fail(nullptr, WP_EUNSUPPORTED, "n[d] > 8192 is not supported");
+    if (!(pb->L[d] > 0.0) || !std::isfinite(pb->L[d]) || !std::isfinite(pb->xmin[d]))
+      return fail(nullptr, WP_EINVAL, "L[d] must be finite and > 0");
+  }
+  if (pb->ndim == 1 && pb->precision == WP_C128 && pb->n[0] > 8192)
+    return fail(nullptr, WP_EUNSUPPORTED, "1-D complex128 lines are limited to 8192 points");
+  if (!(pb->mass > 0.0) || !(pb->hbar > 0.0) || !std::isfinite(pb->dt) || !std::isfinite(pb->t0))
+    return fail(nullptr, WP_EINVAL, "mass and hbar must be > 0; dt and t0 finite");
+  return WP_OK;
+}
+
+}  // namespace
+
+// =================================================================== C ABI
+extern "C" {
+
+const char* wp_status_string(wp_status s) {
+  switch (s) {
+    case WP_OK:
+      return "ok";
+    case WP_EINVAL:
+      return "invalid argument";
+    case WP_EUNSUPPORTED:
+      return "unsupported size or dimension";
+    case WP_ENOMEM:
+      return "out of device memory";
+    case WP_ENONFINITE:
+      return "non-finite norm";
+    case WP_ETIMEOUT:
+      return "device wait timed out";
+    case WP_ECUDA:
+      return "CUDA error";
+    case WP_EBUSY:
+      return "busy";
+  }
+  return "unknown status";
+}
+
+const char* wp_last_error(const wp_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+int wp_kernel_count(void) { return K_NCLASSES; }
+
+const char* wp_kernel_name(int k) { return (k >= 0 && k < K_NCLASSES) ? kClassNames[k] : ""; }
+
+wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
+  if (!out) return fail(nullptr, WP_EINVAL, "out is NULL");
+  *out = nullptr;
+  wp_status st = validate_problem(pb);
+  if (st != WP_OK) return st;
+  wp_handle* h = new (std::nothrow) wp_handle();
+  if (!h) return fail(nullptr, WP_ENOMEM, "host allocation failed");
+  h->pb = *pb;
+  h->stream = (cudaStream_t)stream;
+  h->ndim = pb->ndim;
+  h->f64 = (pb->precision == WP_C128);
+  h->elem = h->f64 ? 16 : 8;
+  Geom& g = h->g;
+  g.ndim = pb->ndim;
+  g.dv = 1.0;
+  for (int d = 0; d < 3; d++) {
+    h->n[d] = d < pb->ndim ? pb->n[d] : 1;
+    g.ln[d] = d < pb->ndim ? ilog2(pb->n[d]) : 0;
+    g.xmin[d] = d < pb->ndim ? pb->xmin[d] : 0.0;
+    g.dx[d] = d < pb->ndim ? pb->L[d] / (double)pb->n[d] : 1.0;
+    g.kscale[d] = d < pb->ndim ? 2.0 * 3.14159265358979323846 / pb->L[d] : 0.0;
+    if (d < pb->ndim) g.dv *= g.dx[d];
+  }
+  g.mass = pb->mass;
+  g.hbar = pb->hbar;
+  g.dt = pb->dt;
+  g.t0 = pb->t0;
+  h->N = h->n[0] * h->n[1] * h->n[2];
+  const size_t bytes = (size_t)h->N * h->elem;
+  auto bail = [&](wp_status s) {
+    g_err = h->err;
+    wp_destroy(h);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->state, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state allocation"));
+  if ((e = cudaMemsetAsync(h->state, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+  if (h->ndim > 1)
+    if ((e = cudaMalloc(&h->scratch, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "scratch allocation"));
+  if (pb->autocorr)
+    if ((e = cudaMalloc(&h->psi0, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "psi0 allocation"));
+  if ((e = cudaMalloc(&h->ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(cuda_fail(h, e, "ctrl allocation"));
+  if ((e = cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
+  if ((e = cudaMalloc(&h->dpot, sizeof(DevPot))) != cudaSuccess) return bail(cuda_fail(h, e, "potential allocation"));
+  memset(&h->hpot, 0, sizeof(DevPot));
+  if ((e = cudaMemcpyAsync(h->dpot, &h->hpot, sizeof(DevPot), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "potential copy"));
+  st = h->f64 ? alloc_tables<double>(h) : alloc_tables<float>(h);
+  if (st != WP_OK) return bail(st);
+  // plans
+  int64_t maxtiles = 1;
+  for (int d = 0; d < h->ndim; d++) {
+    h->plan[d] = make_plan(h, d);
+    if (h->plan[d].ntiles > maxtiles) maxtiles = h->plan[d].ntiles;
+    if (h->ndim > 1 && h->plan[d].smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "axis too long for one tile"));
+  }
+  if (h->ndim > 1) {
+    size_t mx = 0;
+    for (int d = 0; d < h->ndim; d++) mx = std::max(mx, h->plan[d].smem);
+    const int rc = h->f64 ? pass_smem_limit_set<double>(mx) : pass_smem_limit_set<float>(mx);
+    if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
+    if ((e = cudaMalloc(&h->part_pos, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
+      return bail(cuda_fail(h, e, "partials allocation"));
+    if ((e = cudaMalloc(&h->part_mom, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
+      return bail(cuda_fail(h, e, "partials allocation"));
+  } else {
+    const int64_t n = h->n[0];
+    const int E = n <= 2048 ? 8 : 16;
+    const int64_t thr = std::max<int64_t>(1, n / E);
+    h->res_ept = E;
+    h->res_nthreads = (int)((thr + 31) / 32 * 32);
+    if (h->res_nthreads > 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long"));
+    h->res_smem = (size_t)n * h->elem;
+    if (h->res_smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long for shared memory"));
+    const int rc = h->f64 ? res1d_smem_limit_set<double>(h->res_smem) : res1d_smem_limit_set<float>(h->res_smem);
+    if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
+    h->plan[0] = make_plan(h, 0);
+    const int rc2 = h->f64 ? pass_smem_limit_set<double>(h->res_smem) : pass_smem_limit_set<float>(h->res_smem);
+    if (rc2) return bail(cuda_fail(h, (cudaError_t)rc2, "shared-memory limit"));
+  }
+  if ((st = ensure_obs(h, 64)) != WP_OK) return bail(st);
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
+  *out = h;
+  return WP_OK;
+}
+
+wp_status wp_destroy(wp_handle* h) {
+  if (!h) return WP_OK;
+  cudaStreamSynchronize(h->stream);
+  void* ptrs[] = {h->state, h->scratch, h->psi0, h->staging, h->ctrl, h->dpot, h->tabmem,
+                  h->part_pos, h->part_mom, h->obs_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& ep : h->pending) {
+    cudaEventDestroy(ep.a);
+    cudaEventDestroy(ep.b);
+  }
+  for (auto e : h->free_events) cudaEventDestroy(e);
+  delete h;
+  return WP_OK;
+}
+
+wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
+  if (!h || !pot) return fail(h, WP_EINVAL, "NULL argument");
+  if (pot->nterms < 0 || pot->nterms > WP_MAX_TERMS) return fail(h, WP_EINVAL, "nterms out of range");
+  DevPot dp;
+  memset(&dp, 0, sizeof(dp));
+  dp.nterms = pot->nterms;
+  for (int k = 0; k < pot->nterms; k++) {
+    const wp_pot_term& t = pot->term[k];
+    if (t.shape < WP_SHAPE_CONST || t.shape > WP_SHAPE_MORSE) return fail(h, WP_EINVAL, "unknown shape");
+    if (t.env < WP_ENV_NONE || t.env > WP_ENV_SIN2) return fail(h, WP_EINVAL, "unknown envelope");
+    if (t.env != WP_ENV_NONE && !(t.tau > 0.0)) return fail(h, WP_EINVAL, "envelope tau must be > 0");
+    if (t.shape == WP_SHAPE_MORSE) {
+      const int ax = (int)t.a[2];
+      if (ax < 0 || ax >= h->ndim || (double)ax != t.a[2]) return fail(h, WP_EINVAL, "morse axis out of range");
+    }
+    if (t.shape == WP_SHAPE_GAUSS) {
+      if (dp.ngauss >= WP_MAX_GAUSS) return fail(h, WP_EINVAL, "too many Gaussian terms");
+      dp.gauss_term[dp.ngauss++] = k;
+    }
+    dp.term[k] = t;
+  }
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  WP_CUDA(h, cudaMemcpy(h->dpot, &dp, sizeof(dp), cudaMemcpyHostToDevice));
+  h->hpot = dp;
+  return WP_OK;
+}
+
+wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
+  if (!h || !psi) return fail(h, WP_EINVAL, "NULL argument");
+  const size_t bytes128 = (size_t)h->N * 16;
+  if (h->f64) {
+    WP_CUDA(h, cudaMemcpyAsync(h->state, psi, bytes128, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream));
+  } else {
+    const void* src = psi;
+    if (!on_device) {
+      if (!h->staging) WP_CUDA(h, cudaMalloc(&h->staging, bytes128));
+      WP_CUDA(h, cudaMemcpyAsync(h->staging, psi, bytes128, cudaMemcpyHostToDevice, h->stream));
+      src = h->staging;
+    }
+    wp_status st = convert_in<float>(h, src);
+    if (st != WP_OK) return st;
+  }
+  return save_psi0(h);
+}
+
+wp_status wp_get_state(wp_handle* h, void* dst, int on_device) {
+  if (!h || !dst) return fail(h, WP_EINVAL, "NULL argument");
+  const size_t bytes128 = (size_t)h->N * 16;
+  if (h->f64) {
+    WP_CUDA(h, cudaMemcpyAsync(dst, h->state, bytes128, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               h->stream));
+  } else {
+    void* tgt = dst;
+    if (!on_device) {
+      if (!h->staging) WP_CUDA(h, cudaMalloc(&h->staging, bytes128));
+      tgt = h->staging;
+    }
+    wp_status st = convert_out<float>(h, tgt);
+    if (st != WP_OK) return st;
+    if (!on_device)
+      WP_CUDA(h, cudaMemcpyAsync(dst, h->staging, bytes128, cudaMemcpyDeviceToHost, h->stream));
+  }
+  if (!on_device) WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return WP_OK;
+}
+
+wp_status wp_init_gaussian(wp_handle* h, const double x0[3], const double p0[3], const double sigma[3]) {
+  if (!h || !x0 || !p0 || !sigma) return fail(h, WP_EINVAL, "NULL argument");
+  for (int d = 0; d < h->ndim; d++)
+    if (!(sigma[d] > 0.0)) return fail(h, WP_EINVAL, "sigma must be > 0");
+  return h->f64 ? gaussian_impl<double>(h, x0, p0, sigma) : gaussian_impl<float>(h, x0, p0, sigma);
+}
+
+wp_status wp_step(wp_handle* h, int64_t nsteps) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  if (nsteps < 0) return fail(h, WP_EINVAL, "nsteps < 0");
+  if (nsteps == 0) return WP_OK;
+  wp_status st = run_set_step(h, h->host_step);
+  if (st != WP_OK) return st;
+  return h->f64 ? chunk_seq<double>(h, nsteps, false) : chunk_seq<float>(h, nsteps, false);
+}
+
+wp_status wp_observe(wp_handle* h, wp_obs* out) {
+  if (!h || !out) return fail(h, WP_EINVAL, "NULL argument");
+  return h->f64 ? observe_impl<double>(h, out) : observe_impl<float>(h, out);
+}
+
+wp_status wp_run(wp_handle* h, int64_t nt, int64_t nprint, wp_obs* obs, int64_t* nobs) {
+  if (!h || !obs) return fail(h, WP_EINVAL, "NULL argument");
+  if (nt < 1 || nprint <= 0 || nprint > nt) return fail(h, WP_EINVAL, "need 0 < nprint <= nt");
+  return h->f64 ? run_impl<double>(h, nt, nprint, obs, nobs) : run_impl<float>(h, nt, nprint, obs, nobs);
+}
+
+wp_status wp_fft(wp_handle* h, int sign) {
+  if (!h || (sign != 1 && sign != -1)) return fail(h, WP_EINVAL, "sign must be +1 or -1");
+  return h->f64 ? fft_seq<double>(h, sign) : fft_seq<float>(h, sign);
+}
+
+void* wp_state_ptr(wp_handle* h) { return h ? h->state : nullptr; }
+
+int64_t wp_get_step_index(const wp_handle* h) { return h ? h->host_step : 0; }
+
+wp_status wp_set_step_index(wp_handle* h, int64_t s) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  h->host_step = s;
+  return WP_OK;
+}
+
+int64_t wp_launch_count(const wp_handle* h) { return h ? h->launches : 0; }
+
+wp_status wp_profile_enable(wp_handle* h, int enable) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  h->profiling = enable != 0;
+  return WP_OK;
+}
+
+wp_status wp_profile_read(wp_handle* h, int kernel, int64_t* launches, double* total_ms) {
+  if (!h || kernel < 0 || kernel >= K_NCLASSES) return fail(h, WP_EINVAL, "bad kernel class");
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (auto& ep : h->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ep.a, ep.b);
+    h->prof_ms[ep.cls] += ms;
+    h->prof_n[ep.cls] += 1;
+    h->free_events.push_back(ep.a);
+    h->free_events.push_back(ep.b);
+  }
+  h->pending.clear();
+  if (launches) *launches = h->prof_n[kernel];
+  if (total_ms) *total_ms = h->prof_ms[kernel];
+  h->prof_n[kernel] = 0;
+  h->prof_ms[kernel] = 0.0;
+  return WP_OK;
+}
+
+}  // extern "C"

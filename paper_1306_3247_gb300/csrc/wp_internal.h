@@ -1,0 +1,207 @@
+// Internal host/device declarations of the split-operator library.
+#pragma once
+
+#include <cstdint>
+
+#include "wavepacket_gpu.h"
+
+namespace wp {
+
+// Flags of one FFT pass over a tile of lines along one axis. The operations run in
+// this order: IFFT, potential phase, position sums, FFT, kinetic round trip,
+// momentum sums, store.
+enum PassFlags : uint32_t {
+  F_IFFT = 1u << 0,      // inverse FFT along the pass axis
+  F_PHASE = 1u << 1,     // multiply by exp(-i V tau/hbar) (all axes in position space)
+  F_OBS_POS = 1u << 2,   // position-space partial sums (after the phase)
+  F_FFT = 1u << 3,       // forward FFT along the pass axis
+  F_KIN = 1u << 4,       // forward FFT, kinetic factor, inverse FFT (all axes in k space)
+  F_OBS_MOM = 1u << 5,   // momentum-space partial sums (after the forward FFT)
+  F_NO_STORE = 1u << 6,  // keep the tile (used by the momentum sums)
+  F_AUTOCORR = 1u << 7,  // add <psi0|psi> to the position sums
+};
+
+// Partial-sum slots per CTA.
+enum Quantity : int {
+  Q_RHO = 0,       // sum |psi|^2
+  Q_X = 1,         // sum x_d |psi|^2, d = 0..2
+  Q_XX = 4,        // sum x_d^2 |psi|^2
+  Q_V = 7,         // sum V |psi|^2
+  Q_AC_RE = 8,     // sum conj(psi0) psi
+  Q_AC_IM = 9,
+  Q_K = 10,        // sum k_d |psi_hat|^2
+  Q_K2 = 13,       // sum |k|^2 |psi_hat|^2
+  Q_RHOK = 14,     // sum |psi_hat|^2
+  NQ = 16
+};
+
+template <class T>
+struct alignas(2 * sizeof(T)) cx {
+  T re, im;
+};
+
+// Per-handle device control block. The time base lives on the device so that a
+// captured CUDA graph replays correctly for any step index.
+struct Ctrl {
+  int64_t step;                  // step index s of the state (t_s = t0 + s dt)
+  int64_t nobs;                  // observation records written by the current run
+  double t_tab;                  // time of the current potential tables
+  double gphase[WP_MAX_GAUSS];   // f_g(t) tau / hbar for the Gaussian terms
+  double gcoef[WP_MAX_GAUSS];    // f_g(t)
+  int32_t err;                   // first error raised by a kernel (0 = none)
+  int32_t pad;
+};
+
+// Potential descriptor as the kernels read it (same field meaning as wp_potential).
+struct DevPot {
+  int32_t nterms;
+  int32_t ngauss;
+  int32_t gauss_term[WP_MAX_GAUSS];  // indices of the Gaussian terms
+  wp_pot_term term[WP_MAX_TERMS];
+};
+
+// Geometry shared by the kernels of one problem.
+struct Geom {
+  int32_t ndim;
+  int32_t ln[3];       // log2 of the extents (0 for axes >= ndim)
+  double xmin[3], dx[3];
+  double kscale[3];    // 2 pi / L
+  double mass, hbar, dt, t0;
+  double dv;           // cell volume
+};
+
+// Device tables of one axis for precision T.
+template <class T>
+struct AxisTab {
+  cx<T>* W;                   // exp(-2 pi i k/n), k < n (FP64-generated)
+  cx<T>* Kfull;               // exp(-i hbar k^2 dt/2m) (axis 0 also carries 1/N)
+  cx<T>* Khalf;               // the same for dt/2
+  cx<T>* P;                   // exp(-i A(x,t) tau/hbar): additive potential phase
+  cx<T>* W_lo;
+  cx<T>* Kfull_lo;            // low parts: value - (double)high, so that high + low
+  cx<T>* Khalf_lo;            // carries the factor to about twice the precision of T
+  cx<T>* P_lo;
+  T* G[WP_MAX_GAUSS];         // Gaussian-term factors exp(-((x - c)/w)^2)
+  double* A;                  // additive potential A(x,t), FP64
+  double* Gd[WP_MAX_GAUSS];   // Gaussian factors, FP64
+};
+
+template <class T>
+struct PassParams {
+  cx<T>* in;
+  cx<T>* out;
+  const cx<T>* psi0;
+  Geom g;
+  int32_t axis;        // axis the pass transforms
+  int32_t logn;        // log2 of its length
+  int32_t logC;        // log2 of the lines per tile
+  int32_t LS;          // shared-memory row stride in elements (lines are rows' columns)
+  int32_t log_inner;   // log2 of the element stride of the axis (0: contiguous)
+  int32_t nthreads;    // block size; nthreads * ept >= tile elements
+  int32_t ept;         // elements per thread (8 or 16): selects the kernel variant
+  uint32_t flags;
+  int32_t ngauss;
+  int32_t khalf;       // kinetic factor for dt/2 instead of dt
+  const cx<T>* W;
+  const cx<T>* W_lo;
+  const cx<T>* K[3];
+  const cx<T>* K_lo[3];
+  const cx<T>* P[3];
+  const cx<T>* P_lo[3];
+  const T* G[WP_MAX_GAUSS][3];
+  const double* A[3];
+  const double* Gd[WP_MAX_GAUSS][3];
+  const Ctrl* ctrl;
+  double* partials;    // [gridDim.x][NQ]
+};
+
+template <class T>
+struct PrepParams {
+  Geom g;
+  int64_t n[3];
+  AxisTab<T> tab[3];
+  const DevPot* pot;
+  Ctrl* ctrl;
+  int32_t step_add;    // added to ctrl->step before the time is formed
+  double t_shift;      // added to t0 + step dt (dt/2 for the mid-point order)
+  double tau;          // phase length (dt, dt/2 or 0 for observables only)
+};
+
+template <class T>
+struct Res1dParams {
+  cx<T>* psi;
+  const cx<T>* psi0;
+  Geom g;
+  int32_t logn;
+  int32_t nthreads;
+  int32_t ept;         // elements per thread (8 or 16)
+  int32_t order;       // wp_order
+  int32_t obs;         // evaluate observables after the chunk
+  int32_t autocorr;
+  int64_t nsteps;      // steps in this chunk
+  const cx<T>* W;
+  const cx<T>* W_lo;
+  const cx<T>* Kfull;
+  const cx<T>* Khalf;
+  const cx<T>* Kfull_lo;
+  const cx<T>* Khalf_lo;
+  const DevPot* pot;
+  Ctrl* ctrl;
+  double* obs_out;     // [..][16] records; written at ctrl->nobs
+  int64_t obs_cap;
+};
+
+struct ReduceParams {
+  const double* pos;   // [npos][NQ]
+  int64_t npos;
+  const double* mom;   // [nmom][NQ]
+  int64_t nmom;
+  Geom g;
+  int64_t ntotal;      // grid points
+  int32_t autocorr;
+  Ctrl* ctrl;
+  double* obs_out;     // [cap][16]
+  int64_t obs_cap;
+};
+
+template <class T>
+struct ConvParams {
+  const void* src;
+  void* dst;
+  int64_t n;
+  int32_t dir;         // 0: complex128 -> state, 1: state -> complex128
+};
+
+template <class T>
+struct GaussParams {
+  cx<T>* psi;
+  Geom g;
+  double x0[3], p0[3], sigma[3];
+  double pref;
+};
+
+// Launchers (defined per precision in the kernel translation units).
+template <class T> int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* stream);
+template <class T> int launch_prep(const PrepParams<T>& p, void* stream);
+template <class T> int launch_res1d(const Res1dParams<T>& p, size_t smem, void* stream);
+template <class T> int launch_convert(const ConvParams<T>& p, void* stream);
+template <class T> int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream);
+int launch_reduce(const ReduceParams& p, void* stream);
+int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
+int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
+template <class T> int pass_smem_limit_set(size_t smem);
+template <class T> int res1d_smem_limit_set(size_t smem);
+
+// Kernel classes for timing and launch counting.
+enum KernelClass : int {
+  K_PASS_CONTIG = 0,
+  K_PASS_STRIDED = 1,
+  K_PASS_KIN = 2,
+  K_PREP = 3,
+  K_RES1D = 4,
+  K_REDUCE = 5,
+  K_AUX = 6,
+  K_NCLASSES = 7
+};
+
+}  // namespace wp

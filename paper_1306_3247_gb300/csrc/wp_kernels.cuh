@@ -1,0 +1,847 @@
+// Device code of the split-operator step (Sec. 2.1 of arXiv:1306.3247), templated on
+// the real type of the state (double: complex128 form; float: complex64 form).
+//
+// One kernel "pass" loads a tile of lines along one axis into shared memory, applies
+// the operations selected by its flags (inverse FFT, potential phase, position sums,
+// forward FFT, kinetic round trip, momentum sums) and writes the tile back. The FFT is
+// a Stockham autosort transform with radix-8/4/2 butterflies held in registers; every
+// stage reads and writes the tile in shared memory, so a pass touches HBM exactly once
+// for reading and once for writing.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "wp_internal.h"
+
+namespace wp {
+
+// ------------------------------------------------------------------ complex helpers
+template <class T>
+__device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.re = a;
+  r.im = b;
+  return r;
+}
+template <class T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) {
+  return mk(a.re + b.re, a.im + b.im);
+}
+template <class T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) {
+  return mk(a.re - b.re, a.im - b.im);
+}
+template <class T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+// a * conj(b)
+template <class T>
+__device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mk(a.re * b.re + a.im * b.im, a.im * b.re - a.re * b.im);
+}
+// multiply by -i (forward transform) or +i (inverse transform)
+template <class T, bool INV>
+__device__ __forceinline__ cx<T> rot(cx<T> a) {
+  return INV ? mk(-a.im, a.re) : mk(a.im, -a.re);
+}
+
+__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+
+// ------------------------------------------------------------------ butterflies
+// DFT of length R in registers, natural order in and out:
+// X_k = sum_r x_r exp(-+ 2 pi i r k / R) (minus forward, plus inverse).
+template <class T, bool INV>
+__device__ __forceinline__ void dft4(cx<T>& x0, cx<T>& x1, cx<T>& x2, cx<T>& x3) {
+  cx<T> a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = rot<T, INV>(csub(x1, x3));
+  x0 = cadd(a0, a2);
+  x2 = csub(a0, a2);
+  x1 = cadd(a1, a3);
+  x3 = csub(a1, a3);
+}
+
+template <class T, int R, bool INV>
+struct Dft;
+
+template <class T, bool INV>
+struct Dft<T, 2, INV> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    cx<T> a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  }
+};
+
+template <class T, bool INV>
+struct Dft<T, 4, INV> {
+  static __device__ __forceinline__ void run(cx<T>* v) { dft4<T, INV>(v[0], v[1], v[2], v[3]); }
+};
+
+// x / sqrt(2). The nearest float to 1/sqrt(2) is 1.7e-8 (relative) too small; applied to a
+// quarter of the terms of every radix-8 stage that shrinks the norm by about 1e-8 per
+// stage, coherently over the steps. In FP32 the product is therefore formed with a
+// two-part constant hi + lo and the exact rounding error of hi*x (Dekker's two-product
+// through an FMA), which leaves an unbiased, correctly rounded-or-nearly result. The
+// rounded intrinsics keep the compiler from contracting the steps.
+__device__ __forceinline__ double mul_rsqrt2(double x) { return 0.707106781186547524400844362104849039 * x; }
+__device__ __forceinline__ float mul_rsqrt2(float x) {
+  const float hi = 0.70710676908493042f, lo = 1.2101617e-8f;
+  const float p = __fmul_rn(hi, x);
+  const float e = fmaf(hi, x, -p);
+  return __fadd_rn(p, fmaf(lo, x, e));
+}
+
+template <class T, bool INV>
+struct Dft<T, 8, INV> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    // radix-2 split into even and odd radix-4 transforms, combined with w8^k
+    dft4<T, INV>(v[0], v[2], v[4], v[6]);
+    dft4<T, INV>(v[1], v[3], v[5], v[7]);
+    cx<T> o1 = v[3], o2 = v[5], o3 = v[7];
+    cx<T> t1 = INV ? mk(mul_rsqrt2(o1.re - o1.im), mul_rsqrt2(o1.re + o1.im))
+                   : mk(mul_rsqrt2(o1.re + o1.im), mul_rsqrt2(o1.im - o1.re));
+    cx<T> t2 = rot<T, INV>(o2);
+    cx<T> t3 = INV ? mk(-mul_rsqrt2(o3.re + o3.im), mul_rsqrt2(o3.re - o3.im))
+                   : mk(mul_rsqrt2(o3.im - o3.re), -mul_rsqrt2(o3.re + o3.im));
+    cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, t1);
+    v[5] = csub(e1, t1);
+    v[2] = cadd(e2, t2);
+    v[6] = csub(e2, t2);
+    v[3] = cadd(e3, t3);
+    v[7] = csub(e3, t3);
+  }
+};
+
+template <int R>
+struct Log2R;
+template <>
+struct Log2R<2> {
+  static constexpr int v = 1;
+};
+template <>
+struct Log2R<4> {
+  static constexpr int v = 2;
+};
+template <>
+struct Log2R<8> {
+  static constexpr int v = 3;
+};
+
+// Products with a factor stored as high + low parts (FP32 tables). The rounded table
+// entries have |w_h| != 1 by up to 6e-8; the same entries act on the same part of the
+// data every step, so a fixed modulus error accumulates into a steady norm drift. The low
+// part is folded into the FMA chain before the final rounding, so each result is the
+// rounded value of v (w_h + w_l) and the remaining rounding error is unbiased. (Adding
+// v w_l to an already rounded v w_h would lose it: it is below half an ulp.)
+__device__ __forceinline__ cx<float> cmul2(cx<float> v, cx<float> h, cx<float> l) {
+  const float cr = v.re * l.re - v.im * l.im;
+  const float ci = v.re * l.im + v.im * l.re;
+  return mk(fmaf(v.re, h.re, fmaf(-v.im, h.im, cr)), fmaf(v.re, h.im, fmaf(v.im, h.re, ci)));
+}
+// v * conj(h + l)
+__device__ __forceinline__ cx<float> cmulc2(cx<float> v, cx<float> h, cx<float> l) {
+  const float cr = v.re * l.re + v.im * l.im;
+  const float ci = v.im * l.re - v.re * l.im;
+  return mk(fmaf(v.re, h.re, fmaf(v.im, h.im, cr)), fmaf(v.im, h.re, fmaf(-v.re, h.im, ci)));
+}
+
+// Twiddle multiplication v * w (forward) or v * conj(w) (inverse). FP64 uses the
+// table entry directly.
+template <bool INV>
+__device__ __forceinline__ cx<double> twiddle(cx<double> v, const cx<double>* __restrict__ W,
+                                              const cx<double>* __restrict__, int k) {
+  const cx<double> w = W[k];
+  return INV ? cmulc(v, w) : cmul(v, w);
+}
+template <bool INV>
+__device__ __forceinline__ cx<float> twiddle(cx<float> v, const cx<float>* __restrict__ W,
+                                             const cx<float>* __restrict__ Wl, int k) {
+  return INV ? cmulc2(v, W[k], Wl[k]) : cmul2(v, W[k], Wl[k]);
+}
+
+// ------------------------------------------------------------------ tile FFT
+// Shared-memory tile: element i of line l at s[i * LS + l], C = 2^logC lines of
+// n = 2^logn elements. Thread mapping puts lines fastest, so a warp touches
+// consecutive addresses in every stage.
+//
+// One Stockham stage of radix R with current span Ns (Ns = product of the radices of
+// the previous stages): butterfly j reads x[j + r n/R], multiplies by the twiddle
+// w_{Ns R}^{r (j mod Ns)}, transforms, and writes to (j div Ns) Ns R + (j mod Ns) + r Ns.
+// After the last stage the line holds its DFT in natural order.
+template <class T, int R, int E, bool INV>
+__device__ __forceinline__ void fft_stage(cx<T>* s, int logn, int logC, int LS, int logNs,
+                                          const cx<T>* __restrict__ W, const cx<T>* __restrict__ Wl, int tid,
+                                          int nthr) {
+  constexpr int B = E / R;
+  constexpr int LR = Log2R<R>::v;
+  const int C = 1 << logC;
+  const int nR = 1 << (logn - LR);
+  const int total = C << (logn - LR);
+  const int Nsm = (1 << logNs) - 1;
+  const int twlog = logn - logNs - LR;
+  cx<T> v[B][R];
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * nthr;
+    if (bi < total) {
+      const int l = bi & (C - 1), j = bi >> logC;
+#pragma unroll
+      for (int r = 0; r < R; r++) v[b][r] = s[(j + r * nR) * LS + l];
+      if (logNs > 0) {
+        const int jm = j & Nsm;
+#pragma unroll
+        for (int r = 1; r < R; r++) v[b][r] = twiddle<INV>(v[b][r], W, Wl, (r * jm) << twlog);
+      }
+      Dft<T, R, INV>::run(v[b]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * nthr;
+    if (bi < total) {
+      const int l = bi & (C - 1), j = bi >> logC;
+      const int jm = j & Nsm;
+      const int d0 = ((j >> logNs) << (logNs + LR)) + jm;
+#pragma unroll
+      for (int r = 0; r < R; r++) s[(d0 + (r << logNs)) * LS + l] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Whole-line transform of every line of the tile (unnormalised).
+template <class T, int E, bool INV>
+__device__ void fft_tile(cx<T>* s, int logn, int logC, int LS, const cx<T>* __restrict__ W,
+                         const cx<T>* __restrict__ Wl, int tid, int nthr) {
+  int logNs = 0;
+  while (logNs < logn) {
+    const int rem = logn - logNs;
+    if (E >= 8 && (rem >= 5 || rem == 3)) {
+      fft_stage<T, 8, E, INV>(s, logn, logC, LS, logNs, W, Wl, tid, nthr);
+      logNs += 3;
+    } else if (E >= 4 && rem >= 2) {
+      fft_stage<T, 4, E, INV>(s, logn, logC, LS, logNs, W, Wl, tid, nthr);
+      logNs += 2;
+    } else {
+      fft_stage<T, 2, E, INV>(s, logn, logC, LS, logNs, W, Wl, tid, nthr);
+      logNs += 1;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ reductions
+// Fixed-order block sum of NQ doubles; thread 0 of the block receives the totals in
+// out[0..NQ). Every thread must call it. Deterministic for a fixed launch shape.
+__device__ __forceinline__ void block_sum(double (&acc)[NQ], double* out, double (*red)[NQ]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; q++) {
+    double v = acc[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double v = 0.0;
+    for (int w = 0; w < nwarps; w++) v += red[w][threadIdx.x];
+    out[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// Observable record from the position sums qp and momentum sums qm (Tab. 3):
+// 0 t, 1 norm, 2-4 <x>, 5-7 <p>, 8-10 <x^2>, 11 E, 12 E_K, 13 E_V, 14 autocorrelation, 15 step.
+__device__ inline void finish_obs(const double* qp, const double* qm, const Geom& g, int64_t ntotal,
+                                  int autocorr, double t, int64_t step, double* rec) {
+  const double dv = g.dv;
+  const double dvk = dv / (double)ntotal;
+  rec[0] = t;
+  rec[1] = sqrt(qp[Q_RHO] * dv);
+  for (int d = 0; d < 3; d++) {
+    rec[2 + d] = qp[Q_X + d] * dv;
+    rec[5 + d] = g.hbar * qm[Q_K + d] * dvk;
+    rec[8 + d] = qp[Q_XX + d] * dv;
+  }
+  rec[12] = g.hbar * g.hbar / (2.0 * g.mass) * qm[Q_K2] * dvk;
+  rec[13] = qp[Q_V] * dv;
+  rec[11] = rec[12] + rec[13];
+  rec[14] = autocorr ? (qp[Q_AC_RE] * qp[Q_AC_RE] + qp[Q_AC_IM] * qp[Q_AC_IM]) * dv * dv : 0.0;
+  rec[15] = (double)step;
+}
+
+// ------------------------------------------------------------------ potential terms
+// f(t) = A0 + A env(t) sin(omega t + phi)
+__device__ inline double term_coef(const wp_pot_term& tm, double t) {
+  double env = 1.0;
+  if (tm.env == WP_ENV_GAUSS) {
+    const double u = (t - tm.t0) / tm.tau;
+    env = exp(-u * u);
+  } else if (tm.env == WP_ENV_SIN2) {
+    if (t >= tm.t0 && t <= tm.t0 + tm.tau) {
+      const double sv = sin(3.14159265358979323846 * t / tm.tau);
+      env = sv * sv;
+    } else {
+      env = 0.0;
+    }
+  }
+  return tm.A0 + tm.A * env * sin(tm.omega * t + tm.phi);
+}
+
+// Additive (non-Gaussian) shape restricted to axis d: the potential is the sum of
+// these per-axis parts plus the Gaussian products.
+__device__ inline double term_axis_part(const wp_pot_term& tm, int d, double x, double t) {
+  const double u = x - (tm.c0[d] + tm.v[d] * t);
+  switch (tm.shape) {
+    case WP_SHAPE_CONST:
+      return d == 0 ? 1.0 : 0.0;
+    case WP_SHAPE_QUAD:
+      return 0.5 * tm.a[d] * u * u;
+    case WP_SHAPE_LINEAR:
+      return tm.a[d] * u;
+    case WP_SHAPE_MORSE:
+      if ((int)tm.a[2] == d) {
+        const double e = 1.0 - exp(-tm.a[1] * u);
+        return tm.a[0] * e * e;
+      }
+      return 0.0;
+    default:
+      return 0.0;
+  }
+}
+
+__device__ inline double gauss_axis_factor(const wp_pot_term& tm, int d, double x, double t) {
+  if (!(tm.a[d] > 0.0)) return 1.0;
+  const double u = (x - (tm.c0[d] + tm.v[d] * t)) / tm.a[d];
+  return exp(-u * u);
+}
+
+// Index of element i along axis `axis`, outer line index o (axes before) and inner
+// index c (axes after) -> grid indices gi[0..2].
+__device__ __forceinline__ void grid_index(const Geom& g, int axis, int64_t o, int64_t c, int i, int gi[3]) {
+  gi[0] = gi[1] = gi[2] = 0;
+  gi[axis] = i;
+  for (int d = g.ndim - 1; d > axis; d--) {
+    gi[d] = (int)(c & ((1 << g.ln[d]) - 1));
+    c >>= g.ln[d];
+  }
+  for (int d = axis - 1; d >= 0; d--) {
+    gi[d] = (int)(o & ((1 << g.ln[d]) - 1));
+    o >>= g.ln[d];
+  }
+}
+
+__device__ __forceinline__ double wavenumber(const Geom& g, int d, int j) {
+  const int n = 1 << g.ln[d];
+  const int js = j < (n >> 1) ? j : j - n;
+  return g.kscale[d] * (double)js;
+}
+
+// ------------------------------------------------------------------ factor application
+// A phase factor is the product of the pass-axis table entry a (element dependent) and
+// the per-line product L of the other axes' entries; both are stored as high + low parts,
+// L formed in FP64. In FP32 the product a L is first formed as high + low parts
+// (error-free products and sums), then applied to v with a single rounding (cmul2).
+// Two successive roundings (v a, then (v a) L) were measured to leave a norm drift near
+// 1e-8 per step on stationary packets; one rounding of the exact factor leaves 1e-10.
+// In FP64 the plain product is accurate enough.
+__device__ __forceinline__ cx<double> apply_factor(cx<double> v, cx<double> ah, cx<double>, cx<double> Lh,
+                                                   cx<double>) {
+  return cmul(v, cmul(ah, Lh));
+}
+
+// a*b - c*d as s + err, err exact to O(eps^2) (Dekker products through FMA, Knuth sum).
+__device__ __forceinline__ void diff_of_products(float a, float b, float c, float d, float& s, float& err) {
+  const float p = __fmul_rn(a, b), q = __fmul_rn(c, d);
+  const float ep = fmaf(a, b, -p), eq = fmaf(c, d, -q);
+  s = __fsub_rn(p, q);
+  const float bb = __fsub_rn(s, p);
+  const float es = __fadd_rn(__fsub_rn(p, __fsub_rn(s, bb)), __fsub_rn(-q, bb));
+  err = __fadd_rn(__fsub_rn(ep, eq), es);
+}
+
+__device__ __forceinline__ cx<float> apply_factor(cx<float> v, cx<float> ah, cx<float> al, cx<float> Lh,
+                                                  cx<float> Ll) {
+  cx<float> fh, fl;
+  float e;
+  diff_of_products(ah.re, Lh.re, ah.im, Lh.im, fh.re, e);
+  fl.re = e + (fmaf(ah.re, Ll.re, al.re * Lh.re) - fmaf(ah.im, Ll.im, al.im * Lh.im));
+  diff_of_products(ah.re, Lh.im, -ah.im, Lh.re, fh.im, e);
+  fl.im = e + (fmaf(ah.re, Ll.im, al.re * Lh.im) + fmaf(ah.im, Ll.re, al.im * Lh.re));
+  return cmul2(v, fh, fl);
+}
+
+// exp(-i theta) applied to v. In FP32 the factor is written as 1 + (c - 1) - i s with
+// c - 1 = -2 sin^2(theta/2), whose modulus is 1 up to O(eps theta^2).
+__device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th) {
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  return cmul(v, mk(cs, -sn));
+}
+__device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {
+  float sh, ch;
+  sincosf(0.5f * th, &sh, &ch);
+  const cx<float> g = mk(-2.0f * sh * sh, -2.0f * sh * ch);
+  return cadd(v, cmul(v, g));
+}
+
+// Per-line products of the non-pass axes' factors (FP64, split into high and low parts),
+// and of the Gaussian-term factors times their coefficient.
+template <class T>
+__device__ void line_factors(const PassParams<T>& p, const cx<T>* const* H, const cx<T>* const* Lo, bool gauss,
+                             bool contig, int64_t o0, int64_t cb, int C, cx<T>* sLh, cx<T>* sLl,
+                             double (*sGl)[64]) {
+  for (int l = threadIdx.x; l < C; l += blockDim.x) {
+    int gi[3];
+    if (contig)
+      grid_index(p.g, p.axis, o0 + l, 0, 0, gi);
+    else
+      grid_index(p.g, p.axis, o0, cb + l, 0, gi);
+    double r = 1.0, m = 0.0;
+    for (int d = 0; d < p.g.ndim; d++) {
+      if (d == p.axis) continue;
+      const cx<T> hh = H[d][gi[d]], ll = Lo[d][gi[d]];
+      const double fr = (double)hh.re + (double)ll.re, fi = (double)hh.im + (double)ll.im;
+      const double nr = r * fr - m * fi, ni = r * fi + m * fr;
+      r = nr;
+      m = ni;
+    }
+    const T hr = (T)r, hm = (T)m;
+    sLh[l] = mk(hr, hm);
+    sLl[l] = mk((T)(r - (double)hr), (T)(m - (double)hm));
+    if (gauss) {
+      for (int gg = 0; gg < p.ngauss; gg++) {
+        double prod = p.ctrl->gphase[gg];
+        for (int d = 0; d < p.g.ndim; d++)
+          if (d != p.axis) prod *= p.Gd[gg][d][gi[d]];
+        sGl[gg][l] = prod;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ pass kernel
+// E elements per thread; the block has at most 32 E threads, so a tile holds at most
+// 32 E^2 elements (2048 for E = 8, 8192 for E = 16). OBS compiles the partial sums in.
+template <class T, int E, bool OBS>
+__global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32][NQ];
+  __shared__ double tot[NQ];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const int tid = threadIdx.x, nthr = p.nthreads;
+  const int logn = p.logn, logC = p.logC, LS = p.LS;
+  const int n = 1 << logn, C = 1 << logC;
+  const int64_t tile = blockIdx.x;
+  const bool contig = (p.log_inner == 0);
+  int64_t o0, cb;
+  if (contig) {
+    o0 = tile << logC;
+    cb = 0;
+  } else {
+    const int tpo = p.log_inner - logC;
+    o0 = tile >> tpo;
+    cb = (tile & ((int64_t(1) << tpo) - 1)) << logC;
+  }
+  const int ntot = C << logn;
+
+  // load the tile
+  for (int e = tid; e < ntot; e += nthr) {
+    int l, i;
+    int64_t gidx;
+    if (contig) {
+      l = e >> logn;
+      i = e & (n - 1);
+      gidx = ((o0 + l) << logn) + i;
+    } else {
+      i = e >> logC;
+      l = e & (C - 1);
+      gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
+    }
+    s[i * LS + l] = p.in[gidx];
+  }
+  __syncthreads();
+
+  const uint32_t f = p.flags;
+  if (f & F_IFFT) fft_tile<T, E, true>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+
+  __shared__ cx<T> sLh[64], sLl[64];
+  __shared__ double sGl[WP_MAX_GAUSS][64];
+
+  if (f & (F_PHASE | (OBS ? F_OBS_POS : 0u))) {
+    if (f & F_PHASE) {
+      line_factors<T>(p, p.P, p.P_lo, true, contig, o0, cb, C, sLh, sLl, sGl);
+      __syncthreads();
+    }
+    double gco[WP_MAX_GAUSS];
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) gco[gg] = p.ctrl->gcoef[gg];
+    const cx<T>* Pa = p.P[p.axis];
+    const cx<T>* Pal = p.P_lo[p.axis];
+    for (int e = tid; e < ntot; e += nthr) {
+      const int l = e & (C - 1), i = e >> logC;
+      cx<T> v = s[i * LS + l];
+      if (f & F_PHASE) {
+        v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
+        for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, (T)sGl[gg][l] * p.G[gg][p.axis][i]);
+        s[i * LS + l] = v;
+      }
+      if (OBS && (f & F_OBS_POS)) {
+        int gi[3];
+        if (contig)
+          grid_index(p.g, p.axis, o0 + l, 0, i, gi);
+        else
+          grid_index(p.g, p.axis, o0, cb + l, i, gi);
+        const double re = (double)v.re, im = (double)v.im;
+        const double rho = re * re + im * im;
+        acc[Q_RHO] += rho;
+        double V = 0.0;
+        for (int d = 0; d < p.g.ndim; d++) {
+          const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
+          acc[Q_X + d] += x * rho;
+          acc[Q_XX + d] += x * x * rho;
+          V += p.A[d][gi[d]];
+        }
+        for (int gg = 0; gg < p.ngauss; gg++) {
+          double prod = gco[gg];
+          for (int d = 0; d < p.g.ndim; d++) prod *= p.Gd[gg][d][gi[d]];
+          V += prod;
+        }
+        acc[Q_V] += V * rho;
+        if (f & F_AUTOCORR) {
+          int64_t gidx;
+          if (contig)
+            gidx = ((o0 + l) << logn) + i;
+          else
+            gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
+          const cx<T> z = p.psi0[gidx];
+          acc[Q_AC_RE] += (double)z.re * re + (double)z.im * im;
+          acc[Q_AC_IM] += (double)z.re * im - (double)z.im * re;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  if (f & (F_FFT | F_KIN)) fft_tile<T, E, false>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+
+  if (f & ((OBS ? F_OBS_MOM : 0u) | F_KIN)) {
+    if (f & F_KIN) {
+      line_factors<T>(p, p.K, p.K_lo, false, contig, o0, cb, C, sLh, sLl, sGl);
+      __syncthreads();
+    }
+    const cx<T>* Ka = p.K[p.axis];
+    const cx<T>* Kal = p.K_lo[p.axis];
+    for (int e = tid; e < ntot; e += nthr) {
+      const int l = e & (C - 1), i = e >> logC;
+      cx<T> v = s[i * LS + l];
+      if (OBS && (f & F_OBS_MOM)) {
+        int gi[3];
+        if (contig)
+          grid_index(p.g, p.axis, o0 + l, 0, i, gi);
+        else
+          grid_index(p.g, p.axis, o0, cb + l, i, gi);
+        const double re = (double)v.re, im = (double)v.im;
+        const double rho = re * re + im * im;
+        acc[Q_RHOK] += rho;
+        for (int d = 0; d < p.g.ndim; d++) {
+          const double k = wavenumber(p.g, d, gi[d]);
+          acc[Q_K + d] += k * rho;
+          acc[Q_K2] += k * k * rho;
+        }
+      }
+      if (f & F_KIN) s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
+    }
+    __syncthreads();
+    if (f & F_KIN) fft_tile<T, E, true>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+  }
+
+  if (!(f & F_NO_STORE)) {
+    for (int e = tid; e < ntot; e += nthr) {
+      int l, i;
+      int64_t gidx;
+      if (contig) {
+        l = e >> logn;
+        i = e & (n - 1);
+        gidx = ((o0 + l) << logn) + i;
+      } else {
+        i = e >> logC;
+        l = e & (C - 1);
+        gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
+      }
+      p.out[gidx] = s[i * LS + l];
+    }
+  }
+
+  if (OBS && (f & (F_OBS_POS | F_OBS_MOM))) {
+    block_sum(acc, tot, red);
+    if (tid < NQ) p.partials[blockIdx.x * (int64_t)NQ + tid] = tot[tid];
+  }
+}
+
+// ------------------------------------------------------------------ per-step tables
+// One block. Forms t = t0 + (step + step_add) dt + t_shift, stores the new step index,
+// and fills, for every axis, the additive potential A_d(x, t), its phase factor
+// exp(-i A_d tau/hbar) (argument reduced by the FP64 sincos), and the Gaussian-term
+// factors; the Gaussian coefficients f_g(t) and f_g(t) tau/hbar go to the control block.
+template <class T>
+__global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
+  __shared__ int64_t s_step;
+  if (threadIdx.x == 0) s_step = p.ctrl->step + p.step_add;
+  __syncthreads();
+  const int64_t step = s_step;
+  const double t = p.g.t0 + (double)step * p.g.dt + p.t_shift;
+  const DevPot& pot = *p.pot;
+  for (int d = 0; d < p.g.ndim; d++) {
+    const AxisTab<T>& tb = p.tab[d];
+    for (int64_t i = threadIdx.x; i < p.n[d]; i += blockDim.x) {
+      const double x = p.g.xmin[d] + (double)i * p.g.dx[d];
+      double A = 0.0;
+      for (int k = 0; k < pot.nterms; k++) {
+        const wp_pot_term& tm = pot.term[k];
+        if (tm.shape == WP_SHAPE_GAUSS) continue;
+        const double part = term_axis_part(tm, d, x, t);
+        if (part != 0.0) A += term_coef(tm, t) * part;
+      }
+      tb.A[i] = A;
+      double sn, cs;
+      sincos(-A * p.tau / p.g.hbar, &sn, &cs);
+      const T hc = (T)cs, hs = (T)sn;
+      tb.P[i] = mk(hc, hs);
+      tb.P_lo[i] = mk((T)(cs - (double)hc), (T)(sn - (double)hs));
+      for (int gg = 0; gg < pot.ngauss; gg++) {
+        const double gf = gauss_axis_factor(pot.term[pot.gauss_term[gg]], d, x, t);
+        tb.Gd[gg][i] = gf;
+        tb.G[gg][i] = (T)gf;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) {
+      double fc = 0.0;
+      if (gg < pot.ngauss) fc = term_coef(pot.term[pot.gauss_term[gg]], t);
+      p.ctrl->gcoef[gg] = fc;
+      p.ctrl->gphase[gg] = fc * p.tau / p.g.hbar;
+    }
+    p.ctrl->t_tab = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) p.ctrl->step = step;
+}
+
+// ------------------------------------------------------------------ 1-D resident kernel
+// One CTA holds one 1-D line in shared memory for a chunk of steps: the whole step
+// (potential phase, FFT, kinetic factor, inverse FFT) runs without touching HBM.
+template <class T, int E>
+__device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, double t, double tau,
+                                      double* fco, int tid, int nthr) {
+  const DevPot& pot = *p.pot;
+  __syncthreads();
+  if (tid < pot.nterms) fco[tid] = term_coef(pot.term[tid], t);
+  __syncthreads();
+  const int n = 1 << p.logn;
+  for (int i = tid; i < n; i += nthr) {
+    const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
+    double V = 0.0;
+    for (int k = 0; k < pot.nterms; k++) {
+      const wp_pot_term& tm = pot.term[k];
+      const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, t) : term_axis_part(tm, 0, x, t);
+      V += fco[k] * sh;
+    }
+    double sn, cs;
+    sincos(-V * tau / p.g.hbar, &sn, &cs);
+    const T hc = (T)cs, hs = (T)sn;
+    const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
+    s[i] = apply_factor(s[i], mk(hc, hs), mk((T)(cs - (double)hc), (T)(sn - (double)hs)), one, zero);
+  }
+  __syncthreads();
+}
+
+template <class T, int E>
+__device__ void res1d_kinetic(cx<T>* s, const Res1dParams<T>& p, const cx<T>* K, const cx<T>* Klo, int tid,
+                              int nthr) {
+  fft_tile<T, E, false>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
+  const int n = 1 << p.logn;
+  const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
+  for (int i = tid; i < n; i += nthr) s[i] = apply_factor(s[i], K[i], Klo[i], one, zero);
+  __syncthreads();
+  fft_tile<T, E, true>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
+}
+
+template <class T, int E, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_res1d(const Res1dParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32][NQ];
+  __shared__ double qp[NQ], qm[NQ];
+  __shared__ double fco[WP_MAX_TERMS];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const int tid = threadIdx.x, nthr = p.nthreads;
+  const int n = 1 << p.logn;
+  const int64_t s0 = p.ctrl->step;
+  const double dt = p.g.dt;
+  auto tim = [&](int64_t k) { return p.g.t0 + (double)k * dt; };
+
+  for (int i = tid; i < n; i += nthr) s[i] = p.psi[i];
+  __syncthreads();
+
+  const int64_t m = p.nsteps;
+  if (m > 0) {
+    if (p.order == WP_ORDER_VKV) {
+      res1d_potential_phase<T, E>(s, p, tim(s0), 0.5 * dt, fco, tid, nthr);
+      for (int64_t k = 0; k < m; k++) {
+        res1d_kinetic<T, E>(s, p, p.Kfull, p.Kfull_lo, tid, nthr);
+        const bool last = (k == m - 1);
+        res1d_potential_phase<T, E>(s, p, tim(s0 + k + 1), last ? 0.5 * dt : dt, fco, tid, nthr);
+      }
+    } else {
+      res1d_kinetic<T, E>(s, p, p.Khalf, p.Khalf_lo, tid, nthr);
+      for (int64_t k = 0; k < m; k++) {
+        res1d_potential_phase<T, E>(s, p, tim(s0 + k) + 0.5 * dt, dt, fco, tid, nthr);
+        res1d_kinetic<T, E>(s, p, (k == m - 1) ? p.Khalf : p.Kfull, (k == m - 1) ? p.Khalf_lo : p.Kfull_lo, tid, nthr);
+      }
+    }
+  }
+
+  for (int i = tid; i < n; i += nthr) p.psi[i] = s[i];
+
+  if (p.obs) {
+    __syncthreads();
+    const DevPot& pot = *p.pot;
+    const double t = tim(s0 + m);
+    if (tid < pot.nterms) fco[tid] = term_coef(pot.term[tid], t);
+    __syncthreads();
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+    for (int i = tid; i < n; i += nthr) {
+      const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
+      const double re = (double)s[i].re, im = (double)s[i].im;
+      const double rho = re * re + im * im;
+      double V = 0.0;
+      for (int k = 0; k < pot.nterms; k++) {
+        const wp_pot_term& tm = pot.term[k];
+        const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, t) : term_axis_part(tm, 0, x, t);
+        V += fco[k] * sh;
+      }
+      acc[Q_RHO] += rho;
+      acc[Q_X] += x * rho;
+      acc[Q_XX] += x * x * rho;
+      acc[Q_V] += V * rho;
+      if (p.autocorr) {
+        const cx<T> z = p.psi0[i];
+        acc[Q_AC_RE] += (double)z.re * re + (double)z.im * im;
+        acc[Q_AC_IM] += (double)z.re * im - (double)z.im * re;
+      }
+    }
+    block_sum(acc, qp, red);
+    fft_tile<T, E, false>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+    for (int i = tid; i < n; i += nthr) {
+      const double re = (double)s[i].re, im = (double)s[i].im;
+      const double rho = re * re + im * im;
+      const double k = wavenumber(p.g, 0, i);
+      acc[Q_RHOK] += rho;
+      acc[Q_K] += k * rho;
+      acc[Q_K2] += k * k * rho;
+    }
+    block_sum(acc, qm, red);
+    if (tid == 0) {
+      const int64_t slot = p.ctrl->nobs;
+      if (slot < p.obs_cap) {
+        finish_obs(qp, qm, p.g, n, p.autocorr, t, s0 + m, p.obs_out + slot * 16);
+        if (!isfinite(p.obs_out[slot * 16 + 1])) p.ctrl->err = WP_ENONFINITE;
+      }
+      p.ctrl->nobs = slot + 1;
+    }
+  }
+  if (tid == 0) p.ctrl->step = s0 + m;
+}
+
+#ifdef WP_COMMON_KERNELS
+// ------------------------------------------------------------------ reduction kernel
+// One block: sums the per-CTA partials in a fixed order and writes the observable record.
+__global__ void __launch_bounds__(256) k_reduce(const ReduceParams p) {
+  __shared__ double red[32][NQ];
+  __shared__ double qp[NQ], qm[NQ];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  for (int64_t r = threadIdx.x; r < p.npos; r += blockDim.x)
+    for (int q = 0; q < NQ; q++) acc[q] += p.pos[r * NQ + q];
+  block_sum(acc, qp, red);
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  for (int64_t r = threadIdx.x; r < p.nmom; r += blockDim.x)
+    for (int q = 0; q < NQ; q++) acc[q] += p.mom[r * NQ + q];
+  block_sum(acc, qm, red);
+  if (threadIdx.x == 0) {
+    const int64_t slot = p.ctrl->nobs;
+    if (slot < p.obs_cap) {
+      finish_obs(qp, qm, p.g, p.ntotal, p.autocorr, p.ctrl->t_tab, p.ctrl->step, p.obs_out + slot * 16);
+      if (!isfinite(p.obs_out[slot * 16 + 1])) p.ctrl->err = WP_ENONFINITE;
+    }
+    p.ctrl->nobs = slot + 1;
+  }
+}
+
+__global__ void k_set_step(Ctrl* c, int64_t step) {
+  c->step = step;
+  c->nobs = 0;
+  c->err = 0;
+}
+
+__global__ void k_add_step(Ctrl* c, int64_t add) { c->step += add; }
+#endif  // WP_COMMON_KERNELS
+
+// ------------------------------------------------------------------ small kernels
+template <class T>
+__global__ void k_convert(const ConvParams<T> p) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= p.n) return;
+  if (p.dir == 0) {
+    const double2 v = reinterpret_cast<const double2*>(p.src)[i];
+    reinterpret_cast<cx<T>*>(p.dst)[i] = mk((T)v.x, (T)v.y);
+  } else {
+    const cx<T> v = reinterpret_cast<const cx<T>*>(p.src)[i];
+    reinterpret_cast<double2*>(p.dst)[i] = make_double2((double)v.re, (double)v.im);
+  }
+}
+
+// Normalised Gaussian packet of Sec. 4.2, evaluated in FP64.
+template <class T>
+__global__ void k_gaussian(const GaussParams<T> p, int64_t ntotal) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ntotal) return;
+  int gi[3] = {0, 0, 0};
+  int64_t r = idx;
+  for (int d = p.g.ndim - 1; d >= 0; d--) {
+    gi[d] = (int)(r & ((1 << p.g.ln[d]) - 1));
+    r >>= p.g.ln[d];
+  }
+  double re = p.pref, im = 0.0;
+  for (int d = 0; d < p.g.ndim; d++) {
+    const double u = p.g.xmin[d] + (double)gi[d] * p.g.dx[d] - p.x0[d];
+    const double amp = exp(-u * u / (p.sigma[d] * p.sigma[d]));
+    double sn, cs;
+    sincos(p.p0[d] * u / p.g.hbar, &sn, &cs);
+    const double nr = (re * cs - im * sn) * amp, ni = (re * sn + im * cs) * amp;
+    re = nr;
+    im = ni;
+  }
+  p.psi[idx] = mk((T)re, (T)im);
+}
+
+}  // namespace wp

@@ -1,0 +1,98 @@
+// Host launchers of the device kernels for one precision (included by the
+// per-precision translation units).
+#pragma once
+
+#include "wp_kernels.cuh"
+
+namespace wp {
+
+static inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? 0 : (int)e; }
+
+template <class T>
+int pass_smem_limit_set(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, false>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, true>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 16, false>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 16, true>, (cudaFuncAttribute)a, (int)smem);
+  return cuda_status(e);
+}
+
+template <class T>
+int res1d_smem_limit_set(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 8, 256>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 16, 512>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 16, 1024>, (cudaFuncAttribute)a, (int)smem);
+  return cuda_status(e);
+}
+
+// p.ept selects the variant (8 elements per thread: <= 256 threads; 16: <= 512).
+template <class T>
+int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* stream) {
+  const bool obs = (p.flags & (F_OBS_POS | F_OBS_MOM)) != 0;
+  const dim3 grid((unsigned)ntiles), block(p.nthreads);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.ept == 8 && p.nthreads <= 256) {
+    if (obs)
+      k_pass<T, 8, true><<<grid, block, smem, st>>>(p);
+    else
+      k_pass<T, 8, false><<<grid, block, smem, st>>>(p);
+  } else if (p.ept == 16 && p.nthreads <= 512) {
+    if (obs)
+      k_pass<T, 16, true><<<grid, block, smem, st>>>(p);
+    else
+      k_pass<T, 16, false><<<grid, block, smem, st>>>(p);
+  } else {
+    return (int)cudaErrorInvalidConfiguration;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_prep(const PrepParams<T>& p, void* stream) {
+  k_prep<T><<<1, 1024, 0, (cudaStream_t)stream>>>(p);
+  return cuda_status(cudaGetLastError());
+}
+
+// p.ept: 8 elements per thread (<= 256 threads) or 16 (<= 1024 threads).
+template <class T>
+int launch_res1d(const Res1dParams<T>& p, size_t smem, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.ept == 8 && p.nthreads <= 256)
+    k_res1d<T, 8, 256><<<1, p.nthreads, smem, st>>>(p);
+  else if (p.ept == 16 && p.nthreads <= 512)
+    k_res1d<T, 16, 512><<<1, p.nthreads, smem, st>>>(p);
+  else if (p.ept == 16 && p.nthreads <= 1024)
+    k_res1d<T, 16, 1024><<<1, p.nthreads, smem, st>>>(p);
+  else
+    return (int)cudaErrorInvalidConfiguration;
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_convert(const ConvParams<T>& p, void* stream) {
+  const int64_t blocks = (p.n + 255) / 256;
+  if (blocks > 0) k_convert<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream) {
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0) k_gaussian<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p, n);
+  return cuda_status(cudaGetLastError());
+}
+
+#define WP_INSTANTIATE(T)                                                         \
+  template int pass_smem_limit_set<T>(size_t);                                    \
+  template int res1d_smem_limit_set<T>(size_t);                                   \
+  template int launch_pass<T>(const PassParams<T>&, int64_t, size_t, void*);     \
+  template int launch_prep<T>(const PrepParams<T>&, void*);                       \
+  template int launch_res1d<T>(const Res1dParams<T>&, size_t, void*);            \
+  template int launch_convert<T>(const ConvParams<T>&, void*);                    \
+  template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);
+
+}  // namespace wp
