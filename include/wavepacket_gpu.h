@@ -171,6 +171,26 @@ const char* wp_kernel_name(int kernel);
 /* Launches of the library's kernels issued by this handle since creation. */
 int64_t wp_launch_count(const wp_handle* h);
 
+/* Allocation-free moments. The paper has no counterpart of this call: it exists for
+ * callers that cannot call cudaMalloc (a host application whose device memory is held
+ * by its own pool or reserved up front, code in a callback where allocation is not
+ * allowed, a loop that cannot take the synchronisation an allocation may cause).
+ * Computes norm, <x_d> and <x_d^2> (Tab. 3 definitions, FP64 sums) of a caller-owned
+ * complex128 row-major state psi_dev on the grid of `problem`, and writes them to the
+ * host record *out (other fields 0, t = problem->t0). It allocates nothing: the partial
+ * sums go to a fixed 256 KiB device array inside the library, present on every device
+ * that loads it until the process exits. Limit: at most 16,777,216 grid points (e.g.
+ * 256^3); larger grids return WP_EUNSUPPORTED with a message naming the limit.
+ * The first call on a device (with that device current) looks up the array's device
+ * address; make that first call before any stream capture. Every call shares the one
+ * array and overwrites it (no slot needs to start at zero), so calls whose kernels
+ * overlap on the GPU (different streams or host threads) race: serialise them.
+ * Runs on `stream` (NULL = legacy default) and synchronises it before returning.
+ * Errors: WP_EINVAL (NULL argument, extent < 1), WP_EUNSUPPORTED (too many points),
+ * WP_ECUDA; the message is in wp_moments_noalloc_error(). */
+wp_status wp_moments_noalloc(const wp_problem* problem, const void* psi_dev, void* stream, wp_obs* out);
+const char* wp_moments_noalloc_error(void);
+
 /* Release everything the handle owns. NULL is accepted. */
 wp_status wp_destroy(wp_handle* h);
 
