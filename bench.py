@@ -175,7 +175,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c128f"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--nt", type=int, default=200)
     ap.add_argument("--cpu-steps", type=int, default=1)
@@ -254,7 +254,7 @@ def main():
     job_device()
     prof = P.profile_read()
     P.profile(False)
-    elem = 16 if args.precision == "c128" else 8
+    elem = 8 if args.precision == "c64" else 16
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     dom_name, (dom_n, dom_ms) = dom
     avg_s = dom_ms / max(1, dom_n) / 1e3
@@ -271,7 +271,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "c128" else "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"c128": "f64", "c64": "f32", "c128f": "f32x2"}[args.precision],
             "data": "synthetic",
             "config": {"workload": cfg["name"] + f" {args.precision} VKV, {nt} steps, observables every {nprint}",
                        "grid": pb["n"], "dt": pb["dt"], "steps_per_job": nt, "parallelism": "replicas",

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "wp_ff.cuh"
 #include "wp_internal.h"
 
 using namespace wp;
@@ -51,7 +52,7 @@ struct wp_handle {
   int64_t n[3] = {1, 1, 1};
   int64_t N = 1;
   size_t elem = 16;
-  bool f64 = true;
+  int prec = WP_C128;
   void* state = nullptr;
   void* scratch = nullptr;
   void* psi0 = nullptr;
@@ -62,6 +63,7 @@ struct wp_handle {
   void* tabmem = nullptr;
   AxisTab<double> tab64[3]{};
   AxisTab<float> tab32[3]{};
+  AxisTab<ff> tabff[3]{};
   double* part_pos = nullptr;
   double* part_mom = nullptr;
   double* obs_dev = nullptr;
@@ -209,6 +211,23 @@ template <>
 AxisTab<float>* tabs<float>(wp_handle* h) {
   return h->tab32;
 }
+template <>
+AxisTab<ff>* tabs<ff>(wp_handle* h) {
+  return h->tabff;
+}
+
+// Calls f with a value of the real type of the handle's precision.
+template <class F>
+auto dispatch(const wp_handle* h, F&& f) {
+  if (h->prec == WP_C64) return f(float{});
+  if (h->prec == WP_C128_F32X2) return f(ff{});
+  return f(double{});
+}
+#define WP_DISPATCH(h, expr)            \
+  dispatch(h, [&](auto tag_) {          \
+    using T = decltype(tag_);           \
+    return expr;                        \
+  })
 
 template <class T>
 wp_status alloc_tables(wp_handle* h) {
@@ -625,7 +644,8 @@ wp_status gaussian_impl(wp_handle* h, const double* x0, const double* p0, const 
 wp_status validate_problem(const wp_problem* pb) {
   if (!pb) return fail(nullptr, WP_EINVAL, "problem is NULL");
   if (pb->ndim < 1 || pb->ndim > 3) return fail(nullptr, WP_EUNSUPPORTED, "ndim must be 1, 2 or 3");
-  if (pb->precision != WP_C128 && pb->precision != WP_C64) return fail(nullptr, WP_EINVAL, "unknown precision");
+  if (pb->precision != WP_C128 && pb->precision != WP_C64 && pb->precision != WP_C128_F32X2)
+    return fail(nullptr, WP_EINVAL, "unknown precision");
   if (pb->order != WP_ORDER_VKV && pb->order != WP_ORDER_KVK) return fail(nullptr, WP_EINVAL, "unknown order");
   for (int d = 0; d < pb->ndim; d++) {
     if (!is_pow2(pb->n[d]) || pb->n[d] < 2)
@@ -684,8 +704,8 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
   h->pb = *pb;
   h->stream = (cudaStream_t)stream;
   h->ndim = pb->ndim;
-  h->f64 = (pb->precision == WP_C128);
-  h->elem = h->f64 ? 16 : 8;
+  h->prec = pb->precision;
+  h->elem = (h->prec == WP_C64) ? 8 : 16;
   Geom& g = h->g;
   g.ndim = pb->ndim;
   g.dv = 1.0;
@@ -721,7 +741,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
   memset(&h->hpot, 0, sizeof(DevPot));
   if ((e = cudaMemcpyAsync(h->dpot, &h->hpot, sizeof(DevPot), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, e, "potential copy"));
-  st = h->f64 ? alloc_tables<double>(h) : alloc_tables<float>(h);
+  st = WP_DISPATCH(h, alloc_tables<T>(h));
   if (st != WP_OK) return bail(st);
   // plans
   int64_t maxtiles = 1;
@@ -733,7 +753,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
   if (h->ndim > 1) {
     size_t mx = 0;
     for (int d = 0; d < h->ndim; d++) mx = std::max(mx, h->plan[d].smem);
-    const int rc = h->f64 ? pass_smem_limit_set<double>(mx) : pass_smem_limit_set<float>(mx);
+    const int rc = WP_DISPATCH(h, pass_smem_limit_set<T>(mx));
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     if ((e = cudaMalloc(&h->part_pos, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
       return bail(cuda_fail(h, e, "partials allocation"));
@@ -748,10 +768,10 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     if (h->res_nthreads > 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long"));
     h->res_smem = (size_t)n * h->elem;
     if (h->res_smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long for shared memory"));
-    const int rc = h->f64 ? res1d_smem_limit_set<double>(h->res_smem) : res1d_smem_limit_set<float>(h->res_smem);
+    const int rc = WP_DISPATCH(h, res1d_smem_limit_set<T>(h->res_smem));
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     h->plan[0] = make_plan(h, 0);
-    const int rc2 = h->f64 ? pass_smem_limit_set<double>(h->res_smem) : pass_smem_limit_set<float>(h->res_smem);
+    const int rc2 = WP_DISPATCH(h, pass_smem_limit_set<T>(h->res_smem));
     if (rc2) return bail(cuda_fail(h, (cudaError_t)rc2, "shared-memory limit"));
   }
   if ((st = ensure_obs(h, 64)) != WP_OK) return bail(st);
@@ -806,7 +826,7 @@ wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
 wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
   if (!h || !psi) return fail(h, WP_EINVAL, "NULL argument");
   const size_t bytes128 = (size_t)h->N * 16;
-  if (h->f64) {
+  if (h->prec == WP_C128) {
     WP_CUDA(h, cudaMemcpyAsync(h->state, psi, bytes128, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                h->stream));
   } else {
@@ -816,7 +836,7 @@ wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
       WP_CUDA(h, cudaMemcpyAsync(h->staging, psi, bytes128, cudaMemcpyHostToDevice, h->stream));
       src = h->staging;
     }
-    wp_status st = convert_in<float>(h, src);
+    wp_status st = WP_DISPATCH(h, convert_in<T>(h, src));
     if (st != WP_OK) return st;
   }
   return save_psi0(h);
@@ -825,7 +845,7 @@ wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
 wp_status wp_get_state(wp_handle* h, void* dst, int on_device) {
   if (!h || !dst) return fail(h, WP_EINVAL, "NULL argument");
   const size_t bytes128 = (size_t)h->N * 16;
-  if (h->f64) {
+  if (h->prec == WP_C128) {
     WP_CUDA(h, cudaMemcpyAsync(dst, h->state, bytes128, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                h->stream));
   } else {
@@ -834,7 +854,7 @@ wp_status wp_get_state(wp_handle* h, void* dst, int on_device) {
       if (!h->staging) WP_CUDA(h, cudaMalloc(&h->staging, bytes128));
       tgt = h->staging;
     }
-    wp_status st = convert_out<float>(h, tgt);
+    wp_status st = WP_DISPATCH(h, convert_out<T>(h, tgt));
     if (st != WP_OK) return st;
     if (!on_device)
       WP_CUDA(h, cudaMemcpyAsync(dst, h->staging, bytes128, cudaMemcpyDeviceToHost, h->stream));
@@ -847,7 +867,7 @@ wp_status wp_init_gaussian(wp_handle* h, const double x0[3], const double p0[3],
   if (!h || !x0 || !p0 || !sigma) return fail(h, WP_EINVAL, "NULL argument");
   for (int d = 0; d < h->ndim; d++)
     if (!(sigma[d] > 0.0)) return fail(h, WP_EINVAL, "sigma must be > 0");
-  return h->f64 ? gaussian_impl<double>(h, x0, p0, sigma) : gaussian_impl<float>(h, x0, p0, sigma);
+  return WP_DISPATCH(h, gaussian_impl<T>(h, x0, p0, sigma));
 }
 
 wp_status wp_step(wp_handle* h, int64_t nsteps) {
@@ -856,23 +876,23 @@ wp_status wp_step(wp_handle* h, int64_t nsteps) {
   if (nsteps == 0) return WP_OK;
   wp_status st = run_set_step(h, h->host_step);
   if (st != WP_OK) return st;
-  return h->f64 ? chunk_seq<double>(h, nsteps, false) : chunk_seq<float>(h, nsteps, false);
+  return WP_DISPATCH(h, chunk_seq<T>(h, nsteps, false));
 }
 
 wp_status wp_observe(wp_handle* h, wp_obs* out) {
   if (!h || !out) return fail(h, WP_EINVAL, "NULL argument");
-  return h->f64 ? observe_impl<double>(h, out) : observe_impl<float>(h, out);
+  return WP_DISPATCH(h, observe_impl<T>(h, out));
 }
 
 wp_status wp_run(wp_handle* h, int64_t nt, int64_t nprint, wp_obs* obs, int64_t* nobs) {
   if (!h || !obs) return fail(h, WP_EINVAL, "NULL argument");
   if (nt < 1 || nprint <= 0 || nprint > nt) return fail(h, WP_EINVAL, "need 0 < nprint <= nt");
-  return h->f64 ? run_impl<double>(h, nt, nprint, obs, nobs) : run_impl<float>(h, nt, nprint, obs, nobs);
+  return WP_DISPATCH(h, run_impl<T>(h, nt, nprint, obs, nobs));
 }
 
 wp_status wp_fft(wp_handle* h, int sign) {
   if (!h || (sign != 1 && sign != -1)) return fail(h, WP_EINVAL, "sign must be +1 or -1");
-  return h->f64 ? fft_seq<double>(h, sign) : fft_seq<float>(h, sign);
+  return WP_DISPATCH(h, fft_seq<T>(h, sign));
 }
 
 void* wp_state_ptr(wp_handle* h) { return h ? h->state : nullptr; }

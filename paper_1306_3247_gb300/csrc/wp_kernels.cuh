@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "wp_ff.cuh"
 #include "wp_internal.h"
 
 namespace wp {
@@ -49,8 +50,14 @@ __device__ __forceinline__ cx<T> rot(cx<T> a) {
   return INV ? mk(-a.im, a.re) : mk(a.im, -a.re);
 }
 
-__device__ __forceinline__ void sincos_t(double x, double* s, double* c) { sincos(x, s, c); }
-__device__ __forceinline__ void sincos_t(float x, float* s, float* c) { sincosf(x, s, c); }
+// Complex products in float-float: each real part is an error-free dot product of two
+// terms (ff_dot2), cheaper than four ff products and two ff sums.
+__device__ __forceinline__ cx<ff> cmul(cx<ff> a, cx<ff> b) {
+  return mk(ff_dot2(a.re, b.re, a.im, b.im, -1.f), ff_dot2(a.re, b.im, a.im, b.re, 1.f));
+}
+__device__ __forceinline__ cx<ff> cmulc(cx<ff> a, cx<ff> b) {
+  return mk(ff_dot2(a.re, b.re, a.im, b.im, 1.f), ff_dot2(a.im, b.re, a.re, b.im, -1.f));
+}
 
 // ------------------------------------------------------------------ butterflies
 // DFT of length R in registers, natural order in and out:
@@ -88,6 +95,13 @@ struct Dft<T, 4, INV> {
 // through an FMA), which leaves an unbiased, correctly rounded-or-nearly result. The
 // rounded intrinsics keep the compiler from contracting the steps.
 __device__ __forceinline__ double mul_rsqrt2(double x) { return 0.707106781186547524400844362104849039 * x; }
+__device__ __forceinline__ ff mul_rsqrt2(ff x) {
+  const float hi = 0.70710676908493042f, lo = 1.2101617e-8f;
+  const float p = __fmul_rn(hi, x.hi);
+  float e = fmaf(hi, x.hi, -p);
+  e = fmaf(hi, x.lo, fmaf(lo, x.hi, e));
+  return ff_fast_renorm(p, e);
+}
 __device__ __forceinline__ float mul_rsqrt2(float x) {
   const float hi = 0.70710676908493042f, lo = 1.2101617e-8f;
   const float p = __fmul_rn(hi, x);
@@ -158,6 +172,12 @@ template <bool INV>
 __device__ __forceinline__ cx<double> twiddle(cx<double> v, const cx<double>* __restrict__ W,
                                               const cx<double>* __restrict__, int k) {
   const cx<double> w = W[k];
+  return INV ? cmulc(v, w) : cmul(v, w);
+}
+template <bool INV>
+__device__ __forceinline__ cx<ff> twiddle(cx<ff> v, const cx<ff>* __restrict__ W, const cx<ff>* __restrict__,
+                                          int k) {
+  const cx<ff> w = W[k];
   return INV ? cmulc(v, w) : cmul(v, w);
 }
 template <bool INV>
@@ -359,6 +379,10 @@ __device__ __forceinline__ cx<double> apply_factor(cx<double> v, cx<double> ah, 
   return cmul(v, cmul(ah, Lh));
 }
 
+__device__ __forceinline__ cx<ff> apply_factor(cx<ff> v, cx<ff> ah, cx<ff>, cx<ff> Lh, cx<ff>) {
+  return cmul(v, cmul(ah, Lh));
+}
+
 // a*b - c*d as s + err, err exact to O(eps^2) (Dekker products through FMA, Knuth sum).
 __device__ __forceinline__ void diff_of_products(float a, float b, float c, float d, float& s, float& err) {
   const float p = __fmul_rn(a, b), q = __fmul_rn(c, d);
@@ -382,9 +406,35 @@ __device__ __forceinline__ cx<float> apply_factor(cx<float> v, cx<float> ah, cx<
 
 // exp(-i theta) applied to v. In FP32 the factor is written as 1 + (c - 1) - i s with
 // c - 1 = -2 sin^2(theta/2), whose modulus is 1 up to O(eps theta^2).
+// FP64: for |theta| < 1/16 (the usual barrier phase per step) the Taylor series of sin and
+// cos to theta^9 / theta^10 is exact to below 1e-20 relative and costs a dozen FMAs;
+// larger arguments use the library sincos.
 __device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th) {
   double sn, cs;
-  sincos(th, &sn, &cs);
+  if (fabs(th) < 0.0625) {
+    const double z = th * th;
+    sn = th * (1.0 + z * (-1.0 / 6 + z * (1.0 / 120 + z * (-1.0 / 5040 + z * (1.0 / 362880)))));
+    cs = 1.0 + z * (-0.5 + z * (1.0 / 24 + z * (-1.0 / 720 + z * (1.0 / 40320 + z * (-1.0 / 3628800)))));
+  } else {
+    sincos(th, &sn, &cs);
+  }
+  return cmul(v, mk(cs, -sn));
+}
+// Float-float: the same Taylor series in float-float arithmetic for |theta| < 1/16, the
+// FP64 sincos otherwise.
+__device__ __forceinline__ cx<ff> apply_gauss_phase(cx<ff> v, ff th) {
+  ff sn, cs;
+  if (fabsf(th.hi) < 0.0625f) {
+    const ff z = th * th;
+    sn = th * (ff(1.0) + z * (ff(-1.0 / 6) + z * (ff(1.0 / 120) + z * (ff(-1.0 / 5040) + z * ff(1.0 / 362880)))));
+    cs = ff(1.0) + z * (ff(-0.5) + z * (ff(1.0 / 24) + z * (ff(-1.0 / 720) + z * (ff(1.0 / 40320) +
+                                                                                      z * ff(-1.0 / 3628800)))));
+  } else {
+    double s, c;
+    sincos((double)th, &s, &c);
+    sn = ff(s);
+    cs = ff(c);
+  }
   return cmul(v, mk(cs, -sn));
 }
 __device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {

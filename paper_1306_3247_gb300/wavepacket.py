@@ -18,13 +18,13 @@ import numpy as np
 from . import build as _build
 
 WP_OK, WP_EINVAL, WP_EUNSUPPORTED, WP_ENOMEM, WP_ENONFINITE, WP_ETIMEOUT, WP_ECUDA, WP_EBUSY = range(8)
-WP_C128, WP_C64 = 0, 1
+WP_C128, WP_C64, WP_C128_F32X2 = 0, 1, 2
 WP_ORDER_VKV, WP_ORDER_KVK = 0, 1
 WP_MAX_TERMS = 8
 WP_MAX_GAUSS = 2
 SHAPES = {"const": 0, "quad": 1, "linear": 2, "gauss": 3, "morse": 4}
 ENVS = {"none": 0, "gauss": 1, "sin2": 2}
-PRECISIONS = {"c128": WP_C128, "c64": WP_C64}
+PRECISIONS = {"c128": WP_C128, "c64": WP_C64, "c128f": WP_C128_F32X2}
 ORDERS = {"vkv": WP_ORDER_VKV, "kvk": WP_ORDER_KVK}
 
 

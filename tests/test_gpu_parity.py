@@ -40,12 +40,12 @@ def compare_obs(obs, ref, rtol):
 # --------------------------------------------------------------------------- transforms
 @pytest.mark.parametrize("shape", [(2,), (8,), (64,), (1024,), (4096,), (8192,), (2, 4), (64, 32), (8, 1024),
                                    (4, 8, 16), (16, 16, 16), (2, 64, 8), (32, 2, 256)])
-@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("prec", ["c128", "c64", "c128f"])
 def test_fft_matches_oracle(shape, prec):
     nd = len(shape)
     pb = {"ndim": nd, "n": list(shape), "xmin": [0.0] * nd, "L": [1.0] * nd, "dt": 0.1}
     x = W.random_state(shape, seed=sum(shape))
-    tol = 1e-13 if prec == "c128" else 3e-6
+    tol = {"c128": 1e-13, "c64": 3e-6, "c128f": 1e-12}[prec]
     with WPK.Propagator(pb, precision=prec) as P:
         P.set_state(x)
         P.fft(-1)
@@ -57,15 +57,16 @@ def test_fft_matches_oracle(shape, prec):
 
 
 # --------------------------------------------------------------------------- 1-D
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("order", ["vkv", "kvk"])
-def test_1d_driven_trap_c128_1000_steps(order):
+def test_1d_driven_trap_c128_1000_steps(order, prec):
     cfg = W.config_1d_driven_trap(order=order)
     pb, terms = cfg["problem"], cfg["terms"]
     psi0 = O.gaussian(pb, **cfg["init"])
     ref, ref_obs = O.run(pb, terms, psi0, cfg["nt"], cfg["nprint"])
-    with WPK.Propagator(pb, terms, "c128", autocorr=True) as P:
+    with WPK.Propagator(pb, terms, prec, autocorr=True) as P:
         P.init_gaussian(**cfg["init"])
-        assert rel_l2(P.get_state(), psi0) < 1e-15
+        assert rel_l2(P.get_state(), psi0) < (1e-15 if prec == "c128" else 1e-14)
         obs = P.run(cfg["nt"], cfg["nprint"])
         psi = P.get_state()
         assert P.step_index == cfg["nt"]
@@ -88,14 +89,15 @@ def test_1d_driven_trap_c64_1000_steps():
     assert np.max(np.abs(obs["norm"] - obs["norm"][0])) < 1e-5
 
 
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("n", [2, 4, 16, 256, 2048, 8192])
-def test_1d_sizes_and_chunking(n):
+def test_1d_sizes_and_chunking(n, prec):
     pb = {"ndim": 1, "n": [n], "xmin": [-10.0], "L": [20.0], "mass": 1.3, "hbar": 0.9, "dt": 0.003, "t0": 0.25}
     terms = [{"shape": "gauss", "a": [1.2], "c0": [0.5], "v": [0.3], "coef": {"A0": 0.8, "A": 0.2, "omega": 1.1}},
              {"shape": "quad", "a": [0.5], "coef": {"A0": 1.0}}]
     psi0 = W.random_state((n,), seed=n)
     ref = O.propagate(pb, terms, psi0, 23)
-    with WPK.Propagator(pb, terms, "c128") as P:
+    with WPK.Propagator(pb, terms, prec) as P:
         P.set_state(psi0)
         P.step(7)
         P.step(1)
@@ -111,13 +113,14 @@ def small_laser_trap(n=128, order="vkv"):
     return cfg, pb
 
 
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("order", ["vkv", "kvk"])
-def test_2d_laser_trap_c128(order):
+def test_2d_laser_trap_c128(order, prec):
     cfg, pb = small_laser_trap(order=order)
     terms = cfg["terms"]
     psi0 = O.gaussian(pb, **cfg["init"])
     ref, ref_obs = O.run(pb, terms, psi0, 200, 50)
-    with WPK.Propagator(pb, terms, "c128", autocorr=True) as P:
+    with WPK.Propagator(pb, terms, prec, autocorr=True) as P:
         P.set_state(psi0)
         obs = P.run(200, 50)
         psi = P.get_state()
@@ -138,8 +141,9 @@ def test_2d_laser_trap_c64():
     assert np.max(np.abs(obs["norm"] - obs["norm"][0])) < 1e-5
 
 
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("shape", [(2, 2), (4, 1024), (2048, 4), (64, 128)])
-def test_2d_shapes_random_state(shape):
+def test_2d_shapes_random_state(shape, prec):
     pb = {"ndim": 2, "n": list(shape), "xmin": [-4.0, -6.0], "L": [8.0, 12.0], "mass": 0.7, "hbar": 1.0,
           "dt": 0.01, "t0": 0.0}
     terms = [{"shape": "quad", "a": [1.0, 0.5], "coef": {"A0": 1.0, "A": 0.3, "omega": 2.0}},
@@ -148,7 +152,7 @@ def test_2d_shapes_random_state(shape):
                                                            "tau": 0.1}}]
     psi0 = W.random_state(shape, seed=3)
     ref = O.propagate(pb, terms, psi0, 12)
-    with WPK.Propagator(pb, terms, "c128") as P:
+    with WPK.Propagator(pb, terms, prec) as P:
         P.set_state(psi0)
         P.step(5)
         P.step(7)
@@ -161,13 +165,14 @@ def small_barrier(n=64, order="vkv"):
     return cfg, cfg["problem"]
 
 
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("order", ["vkv", "kvk"])
-def test_3d_barrier_c128(order):
+def test_3d_barrier_c128(order, prec):
     cfg, pb = small_barrier(order=order)
     terms = cfg["terms"]
     psi0 = O.gaussian(pb, **cfg["init"])
     ref, ref_obs = O.run(pb, terms, psi0, 60, 20)
-    with WPK.Propagator(pb, terms, "c128", autocorr=True) as P:
+    with WPK.Propagator(pb, terms, prec, autocorr=True) as P:
         P.set_state(psi0)
         obs = P.run(60, 20)
         psi = P.get_state()
@@ -188,8 +193,9 @@ def test_3d_barrier_c64():
     assert np.max(np.abs(obs["norm"] - obs["norm"][0])) < 1e-5
 
 
+@pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("shape", [(2, 2, 2), (4, 8, 16), (16, 4, 2), (8, 2, 512)])
-def test_3d_shapes_random_state(shape):
+def test_3d_shapes_random_state(shape, prec):
     pb = {"ndim": 3, "n": list(shape), "xmin": [-3.0, -4.0, -5.0], "L": [6.0, 8.0, 10.0], "mass": 1.0, "hbar": 1.0,
           "dt": 0.02, "t0": 0.1}
     terms = [{"shape": "quad", "a": [1.0, 2.0, 0.5], "coef": {"A0": 1.0}},
@@ -198,7 +204,7 @@ def test_3d_shapes_random_state(shape):
              {"shape": "morse", "a": [0.3, 1.1, 2.0], "c0": [0.0, 0.0, 0.5], "coef": {"A0": 1.0}}]
     psi0 = W.random_state(shape, seed=5)
     ref = O.propagate(pb, terms, psi0, 9)
-    with WPK.Propagator(pb, terms, "c128") as P:
+    with WPK.Propagator(pb, terms, prec) as P:
         P.set_state(psi0)
         P.step(9)
         assert rel_l2(P.get_state(), ref) < TOL128
