@@ -22,6 +22,7 @@ constexpr int kTileLog = 11;  // target tile: 2048 elements (8 per thread, 256 t
 struct PassPlan {
   int axis = 0;
   int logn = 0, logC = 0, LS = 1, log_inner = 0, nthreads = 32, ept = 8;
+  bool fixed = false;
   int64_t ntiles = 0;
   size_t smem = 0;
 };
@@ -168,6 +169,8 @@ PassPlan make_plan(const wp_handle* h, int axis) {
   p.nthreads = (int)((thr + 31) / 32 * 32);
   p.ntiles = h->N / tile;
   p.smem = (size_t)p.LS * ((size_t)1 << p.logn) * h->elem;
+  p.fixed = (p.logn >= kFixedLogMin && p.logn <= kFixedLogMax && p.logC == kTileLog - p.logn && p.nthreads == 256 &&
+             p.ept == 8);
   return p;
 }
 
@@ -240,10 +243,12 @@ wp_status alloc_tables(wp_handle* h) {
   };
   size_t off[3][4 + 2 * WP_MAX_GAUSS + 1];
   size_t off_lo[3][4];
+  size_t off_st[3];
   for (int d = 0; d < h->ndim; d++) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
     for (int k = 0; k < 4; k++) off_lo[d][k] = add(n * sizeof(cx<T>));
+    off_st[d] = add(n * 16);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][4 + gg] = add(n * sizeof(T));
     off[d][4 + WP_MAX_GAUSS] = add(n * sizeof(double));
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][5 + WP_MAX_GAUSS + gg] = add(n * sizeof(double));
@@ -262,6 +267,7 @@ wp_status alloc_tables(wp_handle* h) {
     tb[d].Khalf_lo = (cx<T>*)(base + off_lo[d][1]);
     tb[d].P_lo = (cx<T>*)(base + off_lo[d][2]);
     tb[d].W_lo = (cx<T>*)(base + off_lo[d][3]);
+    tb[d].Wst = (void*)(base + off_st[d]);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].G[gg] = (T*)(base + off[d][4 + gg]);
     tb[d].A = (double*)(base + off[d][4 + WP_MAX_GAUSS]);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].Gd[gg] = (double*)(base + off[d][5 + WP_MAX_GAUSS + gg]);
@@ -283,6 +289,33 @@ wp_status alloc_tables(wp_handle* h) {
     split();
     WP_CUDA(h, cudaMemcpy(tb[d].W, hi.data(), nb, cudaMemcpyHostToDevice));
     WP_CUDA(h, cudaMemcpy(tb[d].W_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    {
+      // per-stage twiddle records for the fixed-size kernels: 16 bytes each, high part
+      // then (FP32 only) low part
+      const int logn = h->g.ln[d];
+      std::vector<unsigned char> rec(n * 16, 0);
+      const long double pi = 3.141592653589793238462643383279502884L;
+      int ls = 0;
+      while (ls < logn) {
+        const int lr = wp_stage_radix_log(logn, ls);
+        if (ls > 0) {
+          const int off = wp_stage_tw_offset(logn, ls);
+          for (int jm = 0; jm < (1 << ls); jm++)
+            for (int r = 1; r < (1 << lr); r++) {
+              const int64_t k = (int64_t)r * jm * ((int64_t)n >> (ls + lr));
+              const long double a = -2.0L * pi * (long double)k / (long double)n;
+              const double cr = (double)cosl(a), ci = (double)sinl(a);
+              const T hr = (T)cr, hi_ = (T)ci;
+              cx<T> rh{hr, hi_}, rl{(T)(cr - (double)hr), (T)(ci - (double)hi_)};
+              unsigned char* dst = &rec[(size_t)(off + jm * ((1 << lr) - 1) + r - 1) * 16];
+              memcpy(dst, &rh, sizeof(rh));
+              if (sizeof(cx<T>) == 8) memcpy(dst + 8, &rl, sizeof(rl));
+            }
+        }
+        ls += lr;
+      }
+      WP_CUDA(h, cudaMemcpy(tb[d].Wst, rec.data(), rec.size(), cudaMemcpyHostToDevice));
+    }
     const double scale = d == 0 ? 1.0 / (double)h->N : 1.0;
     host_kinetic(h, d, h->pb.dt, scale, re, im);
     split();
@@ -319,6 +352,8 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.khalf = khalf;
   p.W = tb[axis].W;
   p.W_lo = tb[axis].W_lo;
+  p.Wst = tb[axis].Wst;
+  p.fixed = pl.fixed ? 1 : 0;
   for (int d = 0; d < h->ndim; d++) {
     p.K[d] = khalf ? tb[d].Khalf : tb[d].Kfull;
     p.K_lo[d] = khalf ? tb[d].Khalf_lo : tb[d].Kfull_lo;
@@ -503,6 +538,7 @@ wp_status fft_seq(wp_handle* h, int sign) {
     pl.LS = 1;
     pl.log_inner = 0;
     pl.ntiles = 1;
+    pl.fixed = false;
     pl.ept = (int64_t(1) << pl.logn) <= 2048 ? 8 : 16;
     const int64_t thr = std::max<int64_t>(1, (int64_t(1) << pl.logn) / pl.ept);
     pl.nthreads = (int)((thr + 31) / 32 * 32);

@@ -40,6 +40,25 @@ struct alignas(2 * sizeof(T)) cx {
   T re, im;
 };
 
+// Stockham stage plan shared by the device FFT and the host table builder: the stage
+// starting at span 2^logNs of a 2^logn transform has radix 2^wp_stage_radix_log (8 while
+// at least 5 or exactly 3 factors of two remain, then 4, then 2).
+__host__ __device__ constexpr int wp_stage_radix_log(int logn, int logNs) {
+  return (logn - logNs >= 5 || logn - logNs == 3) ? 3 : (logn - logNs >= 2 ? 2 : 1);
+}
+// Offset of a stage's entries in the per-stage twiddle table (Ns (R - 1) entries each,
+// none for the first stage).
+__host__ __device__ constexpr int wp_stage_tw_offset(int logn, int logNs) {
+  int off = 0, ls = 0;
+  while (ls < logNs) {
+    const int lr = wp_stage_radix_log(logn, ls);
+    if (ls > 0) off += (1 << ls) * ((1 << lr) - 1);
+    ls += lr;
+  }
+  return off;
+}
+constexpr int kFixedLogMin = 6, kFixedLogMax = 10;  // fixed-size pass kernels: n = 64..1024
+
 // Per-handle device control block. The time base lives on the device so that a
 // captured CUDA graph replays correctly for any step index.
 struct Ctrl {
@@ -78,6 +97,7 @@ struct AxisTab {
   cx<T>* Khalf;               // the same for dt/2
   cx<T>* P;                   // exp(-i A(x,t) tau/hbar): additive potential phase
   cx<T>* W_lo;
+  void* Wst;                  // per-stage twiddle records (fixed-size kernels), 16 B each
   cx<T>* Kfull_lo;            // low parts: value - (double)high, so that high + low
   cx<T>* Khalf_lo;            // carries the factor to about twice the precision of T
   cx<T>* P_lo;
@@ -104,6 +124,8 @@ struct PassParams {
   int32_t khalf;       // kinetic factor for dt/2 instead of dt
   const cx<T>* W;
   const cx<T>* W_lo;
+  const void* Wst;     // per-stage twiddle records of the pass axis
+  int32_t fixed;       // use the fixed-size kernel (n = 2^logn, 2048-element tiles)
   const cx<T>* K[3];
   const cx<T>* K_lo[3];
   const cx<T>* P[3];
@@ -190,6 +212,9 @@ int launch_reduce(const ReduceParams& p, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);
+// fixed-size pass kernels (their own translation units, wp_fixed_*.cu)
+template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
+template <class T> int fixed_smem_limit_set(size_t smem);
 template <class T> int res1d_smem_limit_set(size_t smem);
 
 // Kernel classes for timing and launch counting.

@@ -257,6 +257,77 @@ __device__ void fft_tile(cx<T>* s, int logn, int logC, int LS, const cx<T>* __re
   }
 }
 
+// ------------------------------------------------------------------ fixed-size tile FFT
+// The same Stockham stages with n, C and the row stride known at compile time. Stage
+// twiddles come from a per-stage table: for the stage with span Ns and radix R, entry
+// jm (R-1) + r - 1 holds w_n^{r jm n/(Ns R)}, so one butterfly reads its R-1 twiddles as
+// consecutive 16-byte records. The stage plan is wp_stage_radix_log, shared with the host
+// code that builds the table.
+template <class T>
+struct alignas(16) TwE {
+  cx<T> w;
+};
+template <>
+struct alignas(16) TwE<float> {
+  cx<float> h, l;
+};
+
+template <bool INV>
+__device__ __forceinline__ cx<double> tw_apply(cx<double> v, const TwE<double>& e) {
+  return INV ? cmulc(v, e.w) : cmul(v, e.w);
+}
+template <bool INV>
+__device__ __forceinline__ cx<ff> tw_apply(cx<ff> v, const TwE<ff>& e) {
+  return INV ? cmulc(v, e.w) : cmul(v, e.w);
+}
+template <bool INV>
+__device__ __forceinline__ cx<float> tw_apply(cx<float> v, const TwE<float>& e) {
+  return INV ? cmulc2(v, e.h, e.l) : cmul2(v, e.h, e.l);
+}
+
+template <class T, int LOGN, int LOGC, int LS, int LOGNS, bool INV>
+__device__ __forceinline__ void stage_fixed(cx<T>* s, const TwE<T>* __restrict__ tw, int tid) {
+  constexpr int LR = wp_stage_radix_log(LOGN, LOGNS);
+  constexpr int R = 1 << LR;
+  constexpr int C = 1 << LOGC;
+  constexpr int NR = 1 << (LOGN - LR);
+  constexpr int NT = (C << LOGN) / 8;
+  constexpr int B = 8 / R;
+  constexpr int NS = 1 << LOGNS;
+  cx<T> v[B][R];
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * NT;
+    const int l = bi & (C - 1), j = bi >> LOGC;
+#pragma unroll
+    for (int r = 0; r < R; r++) v[b][r] = s[(j + r * NR) * LS + l];
+    if (LOGNS > 0) {
+      const TwE<T>* e = tw + (j & (NS - 1)) * (R - 1);
+#pragma unroll
+      for (int r = 1; r < R; r++) v[b][r] = tw_apply<INV>(v[b][r], e[r - 1]);
+    }
+    Dft<T, R, INV>::run(v[b]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * NT;
+    const int l = bi & (C - 1), j = bi >> LOGC;
+    const int d0 = ((j >> LOGNS) << (LOGNS + LR)) + (j & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; r++) s[(d0 + (r << LOGNS)) * LS + l] = v[b][r];
+  }
+  __syncthreads();
+}
+
+template <class T, int LOGN, int LOGC, int LS, bool INV, int LOGNS>
+__device__ __forceinline__ void fft_fixed(cx<T>* s, const TwE<T>* __restrict__ tw, int tid) {
+  if constexpr (LOGNS < LOGN) {
+    stage_fixed<T, LOGN, LOGC, LS, LOGNS, INV>(s, tw + wp_stage_tw_offset(LOGN, LOGNS), tid);
+    fft_fixed<T, LOGN, LOGC, LS, INV, LOGNS + wp_stage_radix_log(LOGN, LOGNS)>(s, tw, tid);
+  }
+}
+
 // ------------------------------------------------------------------ reductions
 // Fixed-order block sum of NQ doubles; thread 0 of the block receives the totals in
 // out[0..NQ). Every thread must call it. Deterministic for a fixed launch shape.
@@ -449,7 +520,7 @@ __device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {
 template <class T>
 __device__ void line_factors(const PassParams<T>& p, const cx<T>* const* H, const cx<T>* const* Lo, bool gauss,
                              bool contig, int64_t o0, int64_t cb, int C, cx<T>* sLh, cx<T>* sLl,
-                             double (*sGl)[64]) {
+                             T (*sGl)[64]) {
   for (int l = threadIdx.x; l < C; l += blockDim.x) {
     int gi[3];
     if (contig)
@@ -473,26 +544,58 @@ __device__ void line_factors(const PassParams<T>& p, const cx<T>* const* H, cons
         double prod = p.ctrl->gphase[gg];
         for (int d = 0; d < p.g.ndim; d++)
           if (d != p.axis) prod *= p.Gd[gg][d][gi[d]];
-        sGl[gg][l] = prod;
+        sGl[gg][l] = (T)prod;
       }
     }
   }
 }
 
 // ------------------------------------------------------------------ pass kernel
-// E elements per thread; the block has at most 32 E threads, so a tile holds at most
-// 32 E^2 elements (2048 for E = 8, 8192 for E = 16). OBS compiles the partial sums in.
-template <class T, int E, bool OBS>
-__global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// Shape of a pass: tile lines C = 2^logC, line length n = 2^logn, shared-memory row
+// stride LS, contiguous or strided axis, block size. DynShape holds them at run time;
+// FixShape makes them compile-time constants so that every index folds and the stage
+// sequence unrolls (used for n = 64..1024, the common grid sizes).
+struct DynShape {
+  int logn, logC, LS, nthr;
+  bool contig;
+  template <class T>
+  __device__ explicit DynShape(const PassParams<T>& p)
+      : logn(p.logn), logC(p.logC), LS(p.LS), nthr(p.nthreads), contig(p.log_inner == 0) {}
+};
+
+template <int LOGN, bool CONTIG>
+struct FixShape {
+  static constexpr int logn = LOGN;
+  static constexpr int logC = 11 - LOGN;                   // 2048-element tiles
+  static constexpr int LS = CONTIG ? (1 << logC) + 1 : (1 << logC);
+  static constexpr int nthr = 256;                         // 8 elements per thread
+  static constexpr bool contig = CONTIG;
+};
+
+// Transforms of the tile: the run-time Stockham loop, or the unrolled fixed-size one with
+// per-stage twiddle tables.
+template <class T, int E, bool INV>
+__device__ __forceinline__ void tile_fft(cx<T>* s, const PassParams<T>& p, const DynShape& sh, int tid) {
+  fft_tile<T, E, INV>(s, sh.logn, sh.logC, sh.LS, p.W, p.W_lo, tid, sh.nthr);
+}
+template <class T, int E, bool INV, int LOGN, bool CONTIG>
+__device__ __forceinline__ void tile_fft(cx<T>* s, const PassParams<T>& p, const FixShape<LOGN, CONTIG>&, int tid) {
+  using SH = FixShape<LOGN, CONTIG>;
+  fft_fixed<T, SH::logn, SH::logC, SH::LS, INV, 0>(s, reinterpret_cast<const TwE<T>*>(p.Wst), tid);
+}
+
+template <class T, int E, bool OBS, class SH>
+__device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, cx<T>* s) {
   __shared__ double red[32][NQ];
   __shared__ double tot[NQ];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const int tid = threadIdx.x, nthr = p.nthreads;
-  const int logn = p.logn, logC = p.logC, LS = p.LS;
+  __shared__ cx<T> sLh[64], sLl[64];
+  __shared__ T sGl[WP_MAX_GAUSS][64];
+  const int tid = threadIdx.x;
+  const int nthr = sh.nthr;
+  const int logn = sh.logn, logC = sh.logC, LS = sh.LS;
   const int n = 1 << logn, C = 1 << logC;
   const int64_t tile = blockIdx.x;
-  const bool contig = (p.log_inner == 0);
+  const bool contig = sh.contig;
   int64_t o0, cb;
   if (contig) {
     o0 = tile << logC;
@@ -504,7 +607,9 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
   }
   const int ntot = C << logn;
 
-  // load the tile
+  // load the tile (contiguous axis: consecutive threads read consecutive points of a
+  // line and transpose into the padded tile; strided axis: consecutive threads read the
+  // C adjacent columns of one row)
   for (int e = tid; e < ntot; e += nthr) {
     int l, i;
     int64_t gidx;
@@ -522,22 +627,17 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
   __syncthreads();
 
   const uint32_t f = p.flags;
-  if (f & F_IFFT) fft_tile<T, E, true>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+  if (f & F_IFFT) tile_fft<T, E, true>(s, p, sh, tid);
 
   double acc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; q++) acc[q] = 0.0;
-
-  __shared__ cx<T> sLh[64], sLl[64];
-  __shared__ double sGl[WP_MAX_GAUSS][64];
 
   if (f & (F_PHASE | (OBS ? F_OBS_POS : 0u))) {
     if (f & F_PHASE) {
       line_factors<T>(p, p.P, p.P_lo, true, contig, o0, cb, C, sLh, sLl, sGl);
       __syncthreads();
     }
-    double gco[WP_MAX_GAUSS];
-    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) gco[gg] = p.ctrl->gcoef[gg];
     const cx<T>* Pa = p.P[p.axis];
     const cx<T>* Pal = p.P_lo[p.axis];
     for (int e = tid; e < ntot; e += nthr) {
@@ -545,7 +645,7 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
       cx<T> v = s[i * LS + l];
       if (f & F_PHASE) {
         v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
-        for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, (T)sGl[gg][l] * p.G[gg][p.axis][i]);
+        for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
         s[i * LS + l] = v;
       }
       if (OBS && (f & F_OBS_POS)) {
@@ -565,7 +665,7 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
           V += p.A[d][gi[d]];
         }
         for (int gg = 0; gg < p.ngauss; gg++) {
-          double prod = gco[gg];
+          double prod = p.ctrl->gcoef[gg];
           for (int d = 0; d < p.g.ndim; d++) prod *= p.Gd[gg][d][gi[d]];
           V += prod;
         }
@@ -585,7 +685,7 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
     __syncthreads();
   }
 
-  if (f & (F_FFT | F_KIN)) fft_tile<T, E, false>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+  if (f & (F_FFT | F_KIN)) tile_fft<T, E, false>(s, p, sh, tid);
 
   if (f & ((OBS ? F_OBS_MOM : 0u) | F_KIN)) {
     if (f & F_KIN) {
@@ -615,7 +715,7 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
       if (f & F_KIN) s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
     }
     __syncthreads();
-    if (f & F_KIN) fft_tile<T, E, true>(s, logn, logC, LS, p.W, p.W_lo, tid, nthr);
+    if (f & F_KIN) tile_fft<T, E, true>(s, p, sh, tid);
   }
 
   if (!(f & F_NO_STORE)) {
@@ -639,6 +739,21 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
     block_sum(acc, tot, red);
     if (tid < NQ) p.partials[blockIdx.x * (int64_t)NQ + tid] = tot[tid];
   }
+}
+
+// E elements per thread; the block has at most 32 E threads, so a tile holds at most
+// 32 E^2 elements (2048 for E = 8, 8192 for E = 16). OBS compiles the partial sums in.
+template <class T, int E, bool OBS>
+__global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_body<T, E, OBS>(p, DynShape(p), reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+// Fixed-size pass: n = 2^LOGN points per line, 2048-element tiles, 256 threads.
+template <class T, int LOGN, bool CONTIG, bool OBS>
+__global__ void __launch_bounds__(256) k_pass_fixed(const PassParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_body<T, 8, OBS>(p, FixShape<LOGN, CONTIG>(), reinterpret_cast<cx<T>*>(smem_raw));
 }
 
 // ------------------------------------------------------------------ per-step tables

@@ -10,7 +10,7 @@ static inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? 0 : (in
 
 template <class T>
 int pass_smem_limit_set(size_t smem) {
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = (cudaError_t)fixed_smem_limit_set<T>(smem);
   const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, false>, (cudaFuncAttribute)a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, true>, (cudaFuncAttribute)a, (int)smem);
@@ -29,12 +29,18 @@ int res1d_smem_limit_set(size_t smem) {
   return cuda_status(e);
 }
 
-// p.ept selects the variant (8 elements per thread: <= 256 threads; 16: <= 512).
+// p.fixed selects the fixed-size kernel (n = 64..1024, 2048-element tiles, 256 threads)
+// for passes without partial sums; otherwise p.ept selects the run-time variant (8 elements per thread: <= 256 threads;
+// 16: <= 512).
 template <class T>
 int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* stream) {
   const bool obs = (p.flags & (F_OBS_POS | F_OBS_MOM)) != 0;
   const dim3 grid((unsigned)ntiles), block(p.nthreads);
   cudaStream_t st = (cudaStream_t)stream;
+  if (p.fixed && !obs) {
+    if (p.nthreads != 256 || p.logC != 11 - p.logn) return (int)cudaErrorInvalidConfiguration;
+    return launch_fixed<T>(p, grid.x, smem, stream);
+  }
   if (p.ept == 8 && p.nthreads <= 256) {
     if (obs)
       k_pass<T, 8, true><<<grid, block, smem, st>>>(p);
