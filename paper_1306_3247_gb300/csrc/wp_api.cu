@@ -32,8 +32,8 @@ struct EventPair {
   int cls;
 };
 
-const char* kClassNames[K_NCLASSES] = {"pass_contig", "pass_strided", "pass_kinetic", "prep_tables",
-                                       "step1d_resident", "reduce_observables", "aux"};
+const char* kClassNames[K_NCLASSES] = {"pass_contig",     "pass_strided",       "pass_kinetic", "prep_tables",
+                                       "step1d_resident", "reduce_observables", "aux",          "line_records"};
 
 int ilog2(int64_t v) {
   int l = 0;
@@ -67,6 +67,9 @@ struct wp_handle {
   AxisTab<ff> tabff[3]{};
   double* part_pos = nullptr;
   double* part_mom = nullptr;
+  void* lines_phase = nullptr;     // LineRec<T>[N / n_last] (potential phase, per step)
+  void* lines_kin[2] = {nullptr, nullptr};  // LineRec<T>[N / n_0] (kinetic factor dt, dt/2)
+  int64_t nlines_phase = 0, nlines_kin = 0;
   double* obs_dev = nullptr;
   int64_t obs_cap = 0;
   PassPlan plan[3];
@@ -160,7 +163,7 @@ PassPlan make_plan(const wp_handle* h, int axis) {
   if (logC > lines_log) logC = lines_log;
   p.logC = logC;
   const int C = 1 << logC;
-  p.LS = contig ? (C > 1 ? C + 1 : 1) : C;
+  p.LS = C;
   const int64_t tile = int64_t(C) << p.logn;
   const int E = tile <= 2048 ? 8 : 16;
   int64_t thr = tile / E;
@@ -244,11 +247,13 @@ wp_status alloc_tables(wp_handle* h) {
   size_t off[3][4 + 2 * WP_MAX_GAUSS + 1];
   size_t off_lo[3][4];
   size_t off_st[3];
+  size_t off_rec[3][3];
   for (int d = 0; d < h->ndim; d++) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
     for (int k = 0; k < 4; k++) off_lo[d][k] = add(n * sizeof(cx<T>));
     off_st[d] = add(n * 16);
+    for (int k = 0; k < 3; k++) off_rec[d][k] = add(n * sizeof(TwE<T>));
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][4 + gg] = add(n * sizeof(T));
     off[d][4 + WP_MAX_GAUSS] = add(n * sizeof(double));
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][5 + WP_MAX_GAUSS + gg] = add(n * sizeof(double));
@@ -268,6 +273,9 @@ wp_status alloc_tables(wp_handle* h) {
     tb[d].P_lo = (cx<T>*)(base + off_lo[d][2]);
     tb[d].W_lo = (cx<T>*)(base + off_lo[d][3]);
     tb[d].Wst = (void*)(base + off_st[d]);
+    tb[d].Prec = (TwE<T>*)(base + off_rec[d][0]);
+    tb[d].Kfull_rec = (TwE<T>*)(base + off_rec[d][1]);
+    tb[d].Khalf_rec = (TwE<T>*)(base + off_rec[d][2]);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].G[gg] = (T*)(base + off[d][4 + gg]);
     tb[d].A = (double*)(base + off[d][4 + WP_MAX_GAUSS]);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].Gd[gg] = (double*)(base + off[d][5 + WP_MAX_GAUSS + gg]);
@@ -317,14 +325,19 @@ wp_status alloc_tables(wp_handle* h) {
       WP_CUDA(h, cudaMemcpy(tb[d].Wst, rec.data(), rec.size(), cudaMemcpyHostToDevice));
     }
     const double scale = d == 0 ? 1.0 / (double)h->N : 1.0;
+    std::vector<TwE<T>> recs(n);
     host_kinetic(h, d, h->pb.dt, scale, re, im);
     split();
+    for (size_t k = 0; k < n; k++) recs[k] = make_rec<T>(re[k], im[k]);
     WP_CUDA(h, cudaMemcpy(tb[d].Kfull, hi.data(), nb, cudaMemcpyHostToDevice));
     WP_CUDA(h, cudaMemcpy(tb[d].Kfull_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    WP_CUDA(h, cudaMemcpy(tb[d].Kfull_rec, recs.data(), n * sizeof(TwE<T>), cudaMemcpyHostToDevice));
     host_kinetic(h, d, 0.5 * h->pb.dt, scale, re, im);
     split();
+    for (size_t k = 0; k < n; k++) recs[k] = make_rec<T>(re[k], im[k]);
     WP_CUDA(h, cudaMemcpy(tb[d].Khalf, hi.data(), nb, cudaMemcpyHostToDevice));
     WP_CUDA(h, cudaMemcpy(tb[d].Khalf_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    WP_CUDA(h, cudaMemcpy(tb[d].Khalf_rec, recs.data(), n * sizeof(TwE<T>), cudaMemcpyHostToDevice));
   }
   return WP_OK;
 }
@@ -367,7 +380,32 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   }
   p.ctrl = h->ctrl;
   p.partials = partials;
+  p.Prec = tb[axis].Prec;
+  p.Krec = khalf ? tb[axis].Khalf_rec : tb[axis].Kfull_rec;
+  p.lines_phase = (const LineRec<T>*)h->lines_phase;
+  p.lines_kin = (const LineRec<T>*)h->lines_kin[khalf ? 1 : 0];
   return p;
+}
+
+// Per-line records of the contiguous (potential) or kinetic pass.
+template <class T>
+wp_status run_lines(wp_handle* h, bool phase, int khalf) {
+  LinesParams<T> p{};
+  AxisTab<T>* tb = tabs<T>(h);
+  p.g = h->g;
+  p.axis = phase ? h->ndim - 1 : 0;
+  p.gauss = phase ? 1 : 0;
+  p.ngauss = h->hpot.ngauss;
+  p.nlines = phase ? h->nlines_phase : h->nlines_kin;
+  for (int d = 0; d < h->ndim; d++) {
+    p.H[d] = phase ? tb[d].P : (khalf ? tb[d].Khalf : tb[d].Kfull);
+    p.Lo[d] = phase ? tb[d].P_lo : (khalf ? tb[d].Khalf_lo : tb[d].Kfull_lo);
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) p.Gd[gg][d] = tb[d].Gd[gg];
+  }
+  p.ctrl = h->ctrl;
+  p.out = (LineRec<T>*)(phase ? h->lines_phase : h->lines_kin[khalf ? 1 : 0]);
+  LaunchScope ls(h, K_LINES);
+  return launch_rc(h, launch_lines<T>(p, h->stream), "line-record kernel");
 }
 
 template <class T>
@@ -381,7 +419,12 @@ wp_status run_pass(wp_handle* h, int axis, uint32_t flags, void* in, void* out, 
 }
 
 template <class T>
-wp_status run_prep(wp_handle* h, int step_add, double t_shift, double tau) {
+wp_status run_lines(wp_handle* h, bool phase, int khalf);
+
+// Per-step tables; with phase_lines also the per-line records of the next potential
+// pass (multi-dimensional problems).
+template <class T>
+wp_status run_prep(wp_handle* h, int step_add, double t_shift, double tau, bool phase_lines = false) {
   PrepParams<T> p{};
   p.g = h->g;
   for (int d = 0; d < 3; d++) p.n[d] = h->n[d];
@@ -392,8 +435,13 @@ wp_status run_prep(wp_handle* h, int step_add, double t_shift, double tau) {
   p.step_add = step_add;
   p.t_shift = t_shift;
   p.tau = tau;
-  LaunchScope ls(h, K_PREP);
-  return launch_rc(h, launch_prep<T>(p, h->stream), "prep kernel");
+  {
+    LaunchScope ls(h, K_PREP);
+    wp_status st = launch_rc(h, launch_prep<T>(p, h->stream), "prep kernel");
+    if (st != WP_OK) return st;
+  }
+  if (phase_lines && h->ndim > 1) return run_lines<T>(h, true, 0);
+  return WP_OK;
 }
 
 wp_status run_set_step(wp_handle* h, int64_t step) {
@@ -501,21 +549,21 @@ wp_status chunk_seq(wp_handle* h, int64_t m, bool obs_end) {
   };
   const uint32_t obsf = obs_end ? (F_OBS_POS | (h->pb.autocorr ? F_AUTOCORR : 0u)) : 0u;
   if (h->pb.order == WP_ORDER_VKV) {
-    if ((st = run_prep<T>(h, 0, 0.0, 0.5 * dt)) != WP_OK) return st;
+    if ((st = run_prep<T>(h, 0, 0.0, 0.5 * dt, true)) != WP_OK) return st;
     if ((st = run_pass<T>(h, Z, F_PHASE | F_FFT, S, S)) != WP_OK) return st;
     if ((st = middle(0)) != WP_OK) return st;
     for (int64_t k = 1; k < m; k++) {
-      if ((st = run_prep<T>(h, 1, 0.0, dt)) != WP_OK) return st;
+      if ((st = run_prep<T>(h, 1, 0.0, dt, true)) != WP_OK) return st;
       if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
       if ((st = middle(0)) != WP_OK) return st;
     }
-    if ((st = run_prep<T>(h, 1, 0.0, 0.5 * dt)) != WP_OK) return st;
+    if ((st = run_prep<T>(h, 1, 0.0, 0.5 * dt, true)) != WP_OK) return st;
     if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | obsf, S, S, h->part_pos)) != WP_OK) return st;
   } else {
     if ((st = run_pass<T>(h, Z, F_FFT, S, S)) != WP_OK) return st;
     if ((st = middle(1)) != WP_OK) return st;
     for (int64_t k = 0; k < m; k++) {
-      if ((st = run_prep<T>(h, k == 0 ? 0 : 1, 0.5 * dt, dt)) != WP_OK) return st;
+      if ((st = run_prep<T>(h, k == 0 ? 0 : 1, 0.5 * dt, dt, true)) != WP_OK) return st;
       if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
       if ((st = middle(k == m - 1 ? 1 : 0)) != WP_OK) return st;
     }
@@ -787,6 +835,16 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     if (h->ndim > 1 && h->plan[d].smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "axis too long for one tile"));
   }
   if (h->ndim > 1) {
+    const size_t rec = h->prec == WP_C64 ? sizeof(LineRec<float>) : sizeof(LineRec<double>);
+    h->nlines_phase = h->N / h->n[h->ndim - 1];
+    h->nlines_kin = h->N / h->n[0];
+    if ((e = cudaMalloc(&h->lines_phase, rec * h->nlines_phase)) != cudaSuccess)
+      return bail(cuda_fail(h, e, "line-record allocation"));
+    for (int k = 0; k < 2; k++)
+      if ((e = cudaMalloc(&h->lines_kin[k], rec * h->nlines_kin)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "line-record allocation"));
+    for (int k = 0; k < 2; k++)
+      if ((st = WP_DISPATCH(h, run_lines<T>(h, false, k))) != WP_OK) return bail(st);
     size_t mx = 0;
     for (int d = 0; d < h->ndim; d++) mx = std::max(mx, h->plan[d].smem);
     const int rc = WP_DISPATCH(h, pass_smem_limit_set<T>(mx));
@@ -819,8 +877,9 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
 wp_status wp_destroy(wp_handle* h) {
   if (!h) return WP_OK;
   cudaStreamSynchronize(h->stream);
-  void* ptrs[] = {h->state, h->scratch, h->psi0, h->staging, h->ctrl, h->dpot, h->tabmem,
-                  h->part_pos, h->part_mom, h->obs_dev};
+  void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
+                  h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
+                  h->lines_kin[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ep : h->pending) {

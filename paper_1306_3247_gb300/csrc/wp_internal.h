@@ -59,6 +59,42 @@ __host__ __device__ constexpr int wp_stage_tw_offset(int logn, int logNs) {
 }
 constexpr int kFixedLogMin = 6, kFixedLogMax = 10;  // fixed-size pass kernels: n = 64..1024
 
+// A table factor as one 16-byte record: the value for FP64 and float-float, the high
+// and low FP32 parts for the complex64 form.
+template <class T>
+struct alignas(16) TwE {
+  cx<T> w;
+};
+template <>
+struct alignas(16) TwE<float> {
+  cx<float> h, l;
+};
+
+// A factor value (FP64) as a 16-byte record of precision T.
+template <class T>
+__host__ __device__ inline TwE<T> make_rec(double re, double im) {
+  TwE<T> r;
+  r.w = cx<T>{(T)re, (T)im};
+  return r;
+}
+template <>
+__host__ __device__ inline TwE<float> make_rec<float>(double re, double im) {
+  TwE<float> r;
+  const float hr = (float)re, hi = (float)im;
+  r.h = cx<float>{hr, hi};
+  r.l = cx<float>{(float)(re - (double)hr), (float)(im - (double)hi)};
+  return r;
+}
+
+// Per-line record of a pass: the product of the other axes' factors (potential phase in
+// the contiguous pass, kinetic factor in the kinetic pass) and, for the potential, the
+// per-line Gaussian-term phase coefficients f_g tau/hbar prod_{d != axis} G_d.
+template <class T>
+struct alignas(16) LineRec {
+  TwE<T> L;
+  T g[WP_MAX_GAUSS];
+};
+
 // Per-handle device control block. The time base lives on the device so that a
 // captured CUDA graph replays correctly for any step index.
 struct Ctrl {
@@ -101,6 +137,9 @@ struct AxisTab {
   cx<T>* Kfull_lo;            // low parts: value - (double)high, so that high + low
   cx<T>* Khalf_lo;            // carries the factor to about twice the precision of T
   cx<T>* P_lo;
+  TwE<T>* Prec;               // the same factors as 16-byte records (fixed-size kernels)
+  TwE<T>* Kfull_rec;
+  TwE<T>* Khalf_rec;
   T* G[WP_MAX_GAUSS];         // Gaussian-term factors exp(-((x - c)/w)^2)
   double* A;                  // additive potential A(x,t), FP64
   double* Gd[WP_MAX_GAUSS];   // Gaussian factors, FP64
@@ -135,6 +174,25 @@ struct PassParams {
   const double* Gd[WP_MAX_GAUSS][3];
   const Ctrl* ctrl;
   double* partials;    // [gridDim.x][NQ]
+  const TwE<T>* Prec;      // pass-axis potential-phase records
+  const TwE<T>* Krec;      // pass-axis kinetic records
+  const LineRec<T>* lines_phase;
+  const LineRec<T>* lines_kin;
+};
+
+// Per-line records of one pass (k_lines).
+template <class T>
+struct LinesParams {
+  Geom g;
+  int32_t axis;            // pass axis; lines run over the other axes
+  int32_t gauss;           // also form the Gaussian-term coefficients
+  int32_t ngauss;
+  int64_t nlines;
+  const cx<T>* H[3];
+  const cx<T>* Lo[3];
+  const double* Gd[WP_MAX_GAUSS][3];
+  const Ctrl* ctrl;
+  LineRec<T>* out;
 };
 
 template <class T>
@@ -208,6 +266,7 @@ template <class T> int launch_prep(const PrepParams<T>& p, void* stream);
 template <class T> int launch_res1d(const Res1dParams<T>& p, size_t smem, void* stream);
 template <class T> int launch_convert(const ConvParams<T>& p, void* stream);
 template <class T> int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream);
+template <class T> int launch_lines(const LinesParams<T>& p, void* stream);
 int launch_reduce(const ReduceParams& p, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
@@ -226,7 +285,8 @@ enum KernelClass : int {
   K_RES1D = 4,
   K_REDUCE = 5,
   K_AUX = 6,
-  K_NCLASSES = 7
+  K_LINES = 7,
+  K_NCLASSES = 8
 };
 
 }  // namespace wp

@@ -263,15 +263,6 @@ __device__ void fft_tile(cx<T>* s, int logn, int logC, int LS, const cx<T>* __re
 // jm (R-1) + r - 1 holds w_n^{r jm n/(Ns R)}, so one butterfly reads its R-1 twiddles as
 // consecutive 16-byte records. The stage plan is wp_stage_radix_log, shared with the host
 // code that builds the table.
-template <class T>
-struct alignas(16) TwE {
-  cx<T> w;
-};
-template <>
-struct alignas(16) TwE<float> {
-  cx<float> h, l;
-};
-
 template <bool INV>
 __device__ __forceinline__ cx<double> tw_apply(cx<double> v, const TwE<double>& e) {
   return INV ? cmulc(v, e.w) : cmul(v, e.w);
@@ -510,9 +501,28 @@ __device__ __forceinline__ cx<ff> apply_gauss_phase(cx<ff> v, ff th) {
 }
 __device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {
   float sh, ch;
-  sincosf(0.5f * th, &sh, &ch);
+  const float h = 0.5f * th;
+  if (fabsf(h) < 0.03125f) {
+    // Taylor series of sin and cos at h (terms to h^7 / h^6 leave < 1e-15 relative)
+    const float z = h * h;
+    sh = h * (1.0f + z * (-1.0f / 6 + z * (1.0f / 120 - z * (1.0f / 5040))));
+    ch = 1.0f + z * (-0.5f + z * (1.0f / 24 - z * (1.0f / 720)));
+  } else {
+    sincosf(h, &sh, &ch);
+  }
   const cx<float> g = mk(-2.0f * sh * sh, -2.0f * sh * ch);
   return cadd(v, cmul(v, g));
+}
+
+// Record forms of apply_factor (fixed-size kernels).
+__device__ __forceinline__ cx<double> apply_factor_rec(cx<double> v, const TwE<double>& a, const TwE<double>& L) {
+  return cmul(v, cmul(a.w, L.w));
+}
+__device__ __forceinline__ cx<ff> apply_factor_rec(cx<ff> v, const TwE<ff>& a, const TwE<ff>& L) {
+  return cmul(v, cmul(a.w, L.w));
+}
+__device__ __forceinline__ cx<float> apply_factor_rec(cx<float> v, const TwE<float>& a, const TwE<float>& L) {
+  return apply_factor(v, a.h, a.l, L.h, L.l);
 }
 
 // Per-line products of the non-pass axes' factors (FP64, split into high and low parts),
@@ -556,6 +566,7 @@ __device__ void line_factors(const PassParams<T>& p, const cx<T>* const* H, cons
 // FixShape makes them compile-time constants so that every index folds and the stage
 // sequence unrolls (used for n = 64..1024, the common grid sizes).
 struct DynShape {
+  static constexpr bool fixed = false;
   int logn, logC, LS, nthr;
   bool contig;
   template <class T>
@@ -565,9 +576,10 @@ struct DynShape {
 
 template <int LOGN, bool CONTIG>
 struct FixShape {
+  static constexpr bool fixed = true;                      // reads per-line records
   static constexpr int logn = LOGN;
   static constexpr int logC = 11 - LOGN;                   // 2048-element tiles
-  static constexpr int LS = CONTIG ? (1 << logC) + 1 : (1 << logC);
+  static constexpr int LS = 1 << logC;
   static constexpr int nthr = 256;                         // 8 elements per thread
   static constexpr bool contig = CONTIG;
 };
@@ -590,6 +602,7 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
   __shared__ double tot[NQ];
   __shared__ cx<T> sLh[64], sLl[64];
   __shared__ T sGl[WP_MAX_GAUSS][64];
+  __shared__ LineRec<T> sRec[64];
   const int tid = threadIdx.x;
   const int nthr = sh.nthr;
   const int logn = sh.logn, logC = sh.logC, LS = sh.LS;
@@ -607,21 +620,12 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
   }
   const int ntot = C << logn;
 
-  // load the tile (contiguous axis: consecutive threads read consecutive points of a
-  // line and transpose into the padded tile; strided axis: consecutive threads read the
-  // C adjacent columns of one row)
+  // load the tile with the lines fastest: a warp reads 32 / C consecutive points of each
+  // of C lines (contiguous axis: C separate full sectors; strided axis: one row segment
+  // of C adjacent columns), and writes consecutive shared-memory words
   for (int e = tid; e < ntot; e += nthr) {
-    int l, i;
-    int64_t gidx;
-    if (contig) {
-      l = e >> logn;
-      i = e & (n - 1);
-      gidx = ((o0 + l) << logn) + i;
-    } else {
-      i = e >> logC;
-      l = e & (C - 1);
-      gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
-    }
+    const int i = e >> logC, l = e & (C - 1);
+    const int64_t gidx = contig ? ((o0 + l) << logn) + i : (((o0 << logn) + i) << p.log_inner) + cb + l;
     s[i * LS + l] = p.in[gidx];
   }
   __syncthreads();
@@ -635,7 +639,11 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
 
   if (f & (F_PHASE | (OBS ? F_OBS_POS : 0u))) {
     if (f & F_PHASE) {
-      line_factors<T>(p, p.P, p.P_lo, true, contig, o0, cb, C, sLh, sLl, sGl);
+      if constexpr (SH::fixed) {
+        for (int l = tid; l < C; l += nthr) sRec[l] = p.lines_phase[contig ? o0 + l : cb + l];
+      } else {
+        line_factors<T>(p, p.P, p.P_lo, true, contig, o0, cb, C, sLh, sLl, sGl);
+      }
       __syncthreads();
     }
     const cx<T>* Pa = p.P[p.axis];
@@ -644,8 +652,13 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
       if (f & F_PHASE) {
-        v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
-        for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
+        if constexpr (SH::fixed) {
+          v = apply_factor_rec(v, p.Prec[i], sRec[l].L);
+          for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sRec[l].g[gg] * p.G[gg][p.axis][i]);
+        } else {
+          v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
+          for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
+        }
         s[i * LS + l] = v;
       }
       if (OBS && (f & F_OBS_POS)) {
@@ -689,7 +702,11 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
 
   if (f & ((OBS ? F_OBS_MOM : 0u) | F_KIN)) {
     if (f & F_KIN) {
-      line_factors<T>(p, p.K, p.K_lo, false, contig, o0, cb, C, sLh, sLl, sGl);
+      if constexpr (SH::fixed) {
+        for (int l = tid; l < C; l += nthr) sRec[l] = p.lines_kin[contig ? o0 + l : cb + l];
+      } else {
+        line_factors<T>(p, p.K, p.K_lo, false, contig, o0, cb, C, sLh, sLl, sGl);
+      }
       __syncthreads();
     }
     const cx<T>* Ka = p.K[p.axis];
@@ -712,7 +729,12 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
           acc[Q_K2] += k * k * rho;
         }
       }
-      if (f & F_KIN) s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
+      if (f & F_KIN) {
+        if constexpr (SH::fixed)
+          s[i * LS + l] = apply_factor_rec(v, p.Krec[i], sRec[l].L);
+        else
+          s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
+      }
     }
     __syncthreads();
     if (f & F_KIN) tile_fft<T, E, true>(s, p, sh, tid);
@@ -720,17 +742,8 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
 
   if (!(f & F_NO_STORE)) {
     for (int e = tid; e < ntot; e += nthr) {
-      int l, i;
-      int64_t gidx;
-      if (contig) {
-        l = e >> logn;
-        i = e & (n - 1);
-        gidx = ((o0 + l) << logn) + i;
-      } else {
-        i = e >> logC;
-        l = e & (C - 1);
-        gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
-      }
+      const int i = e >> logC, l = e & (C - 1);
+      const int64_t gidx = contig ? ((o0 + l) << logn) + i : (((o0 << logn) + i) << p.log_inner) + cb + l;
       p.out[gidx] = s[i * LS + l];
     }
   }
@@ -754,6 +767,44 @@ template <class T, int LOGN, bool CONTIG, bool OBS>
 __global__ void __launch_bounds__(256) k_pass_fixed(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pass_body<T, 8, OBS>(p, FixShape<LOGN, CONTIG>(), reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+// ------------------------------------------------------------------ per-line records
+// One record per line of a pass: the FP64 product of the other axes' factors (high +
+// low table parts), rounded to a record, and the per-line Gaussian-term phase
+// coefficients. Grid-stride over the lines.
+template <class T>
+__global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
+  const bool contig = (p.axis == p.g.ndim - 1);
+  for (int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; line < p.nlines;
+       line += (int64_t)gridDim.x * blockDim.x) {
+    int gi[3];
+    if (contig)
+      grid_index(p.g, p.axis, line, 0, 0, gi);
+    else
+      grid_index(p.g, p.axis, 0, line, 0, gi);
+    double r = 1.0, m = 0.0;
+    for (int d = 0; d < p.g.ndim; d++) {
+      if (d == p.axis) continue;
+      const cx<T> hh = p.H[d][gi[d]], ll = p.Lo[d][gi[d]];
+      const double fr = (double)hh.re + (double)ll.re, fi = (double)hh.im + (double)ll.im;
+      const double nr = r * fr - m * fi, ni = r * fi + m * fr;
+      r = nr;
+      m = ni;
+    }
+    LineRec<T> rec;
+    rec.L = make_rec<T>(r, m);
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) {
+      double prod = 0.0;
+      if (p.gauss && gg < p.ngauss) {
+        prod = p.ctrl->gphase[gg];
+        for (int d = 0; d < p.g.ndim; d++)
+          if (d != p.axis) prod *= p.Gd[gg][d][gi[d]];
+      }
+      rec.g[gg] = (T)prod;
+    }
+    p.out[line] = rec;
+  }
 }
 
 // ------------------------------------------------------------------ per-step tables
@@ -786,6 +837,7 @@ __global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
       const T hc = (T)cs, hs = (T)sn;
       tb.P[i] = mk(hc, hs);
       tb.P_lo[i] = mk((T)(cs - (double)hc), (T)(sn - (double)hs));
+      tb.Prec[i] = make_rec<T>(cs, sn);
       for (int gg = 0; gg < pot.ngauss; gg++) {
         const double gf = gauss_axis_factor(pot.term[pot.gauss_term[gg]], d, x, t);
         tb.Gd[gg][i] = gf;

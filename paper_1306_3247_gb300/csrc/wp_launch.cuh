@@ -92,6 +92,14 @@ int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream) {
   return cuda_status(cudaGetLastError());
 }
 
+template <class T>
+int launch_lines(const LinesParams<T>& p, void* stream) {
+  int64_t blocks = (p.nlines + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks > 0) k_lines<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+  return cuda_status(cudaGetLastError());
+}
+
 #define WP_INSTANTIATE(T)                                                         \
   template int pass_smem_limit_set<T>(size_t);                                    \
   template int res1d_smem_limit_set<T>(size_t);                                   \
@@ -99,6 +107,7 @@ int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream) {
   template int launch_prep<T>(const PrepParams<T>&, void*);                       \
   template int launch_res1d<T>(const Res1dParams<T>&, size_t, void*);            \
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
-  template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);
+  template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
+  template int launch_lines<T>(const LinesParams<T>&, void*);
 
 }  // namespace wp
