@@ -160,7 +160,8 @@ wp_status wp_fft(wp_handle* h, int sign);
  * point (re_hi, re_lo, im_hi, im_lo), row-major. */
 void* wp_state_ptr(wp_handle* h);
 
-/* Current step index s (t_s = t0 + s dt); settable for checkpoint/resume. */
+/* Current step index s (t_s = t0 + s dt); settable for checkpoint/resume (the setter
+ * also updates the device copy, ordered on the handle's stream). */
 int64_t wp_get_step_index(const wp_handle* h);
 wp_status wp_set_step_index(wp_handle* h, int64_t s);
 
@@ -175,6 +176,27 @@ const char* wp_kernel_name(int kernel);
 
 /* Launches of the library's kernels issued by this handle since creation. */
 int64_t wp_launch_count(const wp_handle* h);
+
+/* Batched instances (many independent propagations, e.g. uneven 1-D and 2-D grids).
+ * A batch owns its instances' handles, all on one stream (the given one, or a new
+ * non-blocking stream for NULL). wp_batch_add creates an instance (its precision must be
+ * the batch's) and returns its index; wp_batch_handle gives the borrowed handle for
+ * wp_init_gaussian / wp_set_state / wp_get_state / wp_observe (valid until
+ * wp_batch_destroy). wp_batch_step advances every instance by nsteps steps (the chunk
+ * semantics of wp_step): 1-D instances run in one resident launch per line length for
+ * the whole chunk, 2-D instances whose axes tile into 2048-point tiles share one launch
+ * per pass kind per step, others run their own sequence. With use_graph != 0 the chunk
+ * is captured once per chunk length as a CUDA graph (on its second use) and replayed.
+ * Each instance's result equals what the instance gives alone. */
+typedef struct wp_batch wp_batch;
+wp_status wp_batch_create(int32_t precision, void* stream, wp_batch** out);
+wp_status wp_batch_add(wp_batch* b, const wp_problem* problem, const wp_potential* pot, int64_t* index);
+wp_handle* wp_batch_handle(wp_batch* b, int64_t index);
+int64_t wp_batch_size(const wp_batch* b);
+wp_status wp_batch_step(wp_batch* b, int64_t nsteps, int use_graph);
+int64_t wp_batch_launch_count(const wp_batch* b);  /* kernel launches issued (graph replays count 0) */
+wp_status wp_batch_destroy(wp_batch* b);
+const char* wp_batch_last_error(const wp_batch* b);
 
 /* Allocation-free moments. The paper has no counterpart of this call: it exists for
  * callers that cannot call cudaMalloc (a host application whose device memory is held

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -747,6 +748,265 @@ wp_status validate_problem(const wp_problem* pb) {
 
 }  // namespace
 
+// =================================================================== batched instances
+// A batch owns many handles on one stream. 2-D instances whose passes tile into
+// 2048-element tiles are advanced by batched kernels (one launch per pass kind per step
+// for all of them), 1-D instances by one resident launch per line length for the whole
+// chunk, anything else by its own sequence. The step sequence can be captured once per
+// chunk length as a CUDA graph and replayed.
+struct BatchClass1D {
+  int logn = 0, nthreads = 32, ept = 8;
+  size_t smem = 0;
+  std::vector<int> idx;
+  void* dparams = nullptr;
+};
+
+struct wp_batch {
+  int prec = WP_C128;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<wp_handle*> inst;
+  bool dirty = true;
+  int order2d = WP_ORDER_VKV;
+  std::vector<int> idx2d, idx_other;
+  std::vector<BatchClass1D> classes1d;
+  void* d_pass_z = nullptr;
+  void* d_pass_x = nullptr;
+  void* d_prep = nullptr;
+  int64_t* d_tiles_z = nullptr;
+  int64_t* d_tiles_x = nullptr;
+  int64_t ntiles_z = 0, ntiles_x = 0;
+  size_t smem2d = 0;
+  std::map<int64_t, cudaGraphExec_t> graphs;
+  std::map<int64_t, int> seen;  // chunk lengths run once without a graph
+  int64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+wp_status bfail(wp_batch* b, wp_status st, const std::string& m) {
+  if (b) b->err = m;
+  return st;
+}
+
+void batch_free_compiled(wp_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+  b->seen.clear();
+  void* ps[] = {b->d_pass_z, b->d_pass_x, b->d_prep, b->d_tiles_z, b->d_tiles_x};
+  for (void* q : ps)
+    if (q) cudaFree(q);
+  b->d_pass_z = b->d_pass_x = b->d_prep = nullptr;
+  b->d_tiles_z = b->d_tiles_x = nullptr;
+  for (auto& c : b->classes1d)
+    if (c.dparams) cudaFree(c.dparams);
+  b->classes1d.clear();
+  b->idx2d.clear();
+  b->idx_other.clear();
+}
+
+bool batchable_2d(const wp_handle* h) {
+  if (h->ndim != 2) return false;
+  for (int d = 0; d < 2; d++) {
+    const PassPlan& pl = h->plan[d];
+    if (pl.nthreads != 256 || pl.ept != 8 || ((int64_t)1 << (pl.logn + pl.logC)) != 2048) return false;
+  }
+  return true;
+}
+
+template <class T>
+wp_status batch_compile(wp_batch* b) {
+  batch_free_compiled(b);
+  std::map<int, BatchClass1D> cls;
+  for (int k = 0; k < (int)b->inst.size(); k++) {
+    wp_handle* h = b->inst[k];
+    if (h->ndim == 1) {
+      BatchClass1D& c = cls[h->g.ln[0]];
+      c.logn = h->g.ln[0];
+      c.nthreads = h->res_nthreads;
+      c.ept = h->res_ept;
+      c.smem = h->res_smem;
+      c.idx.push_back(k);
+    } else if (batchable_2d(h) && (b->idx2d.empty() || h->pb.order == b->order2d)) {
+      if (b->idx2d.empty()) b->order2d = h->pb.order;
+      b->idx2d.push_back(k);
+    } else {
+      b->idx_other.push_back(k);
+    }
+  }
+  for (auto& kv : cls) {
+    BatchClass1D c = kv.second;
+    std::vector<Res1dParams<T>> ps;
+    for (int k : c.idx) {
+      wp_handle* h = b->inst[k];
+      AxisTab<T>* tb = tabs<T>(h);
+      Res1dParams<T> p{};
+      p.psi = (cx<T>*)h->state;
+      p.psi0 = (const cx<T>*)h->psi0;
+      p.g = h->g;
+      p.logn = h->g.ln[0];
+      p.nthreads = h->res_nthreads;
+      p.ept = h->res_ept;
+      p.order = h->pb.order;
+      p.autocorr = h->pb.autocorr ? 1 : 0;
+      p.W = tb[0].W;
+      p.W_lo = tb[0].W_lo;
+      p.Kfull = tb[0].Kfull;
+      p.Khalf = tb[0].Khalf;
+      p.Kfull_lo = tb[0].Kfull_lo;
+      p.Khalf_lo = tb[0].Khalf_lo;
+      p.pot = h->dpot;
+      p.ctrl = h->ctrl;
+      p.obs_out = h->obs_dev;
+      p.obs_cap = h->obs_cap;
+      ps.push_back(p);
+    }
+    WP_CUDA(nullptr, cudaMalloc(&c.dparams, ps.size() * sizeof(Res1dParams<T>)));
+    WP_CUDA(nullptr, cudaMemcpy(c.dparams, ps.data(), ps.size() * sizeof(Res1dParams<T>), cudaMemcpyHostToDevice));
+    b->classes1d.push_back(c);
+  }
+  if (!b->idx2d.empty()) {
+    std::vector<PassParams<T>> pz, px;
+    std::vector<PrepParams<T>> pp;
+    std::vector<int64_t> tz, tx;
+    int64_t az = 0, ax = 0;
+    for (int k : b->idx2d) {
+      wp_handle* h = b->inst[k];
+      AxisTab<T>* tb = tabs<T>(h);
+      PassParams<T> qz = pass_params<T>(h, 1, 0, h->state, h->state, nullptr, 0);
+      PassParams<T> qx = pass_params<T>(h, 0, 0, h->state, h->state, nullptr, 0);
+      qz.fixed = qx.fixed = 0;
+      for (int d = 0; d < 2; d++) {
+        qx.Khalf_axes[d] = tb[d].Khalf;
+        qx.Khalf_lo_axes[d] = tb[d].Khalf_lo;
+      }
+      pz.push_back(qz);
+      px.push_back(qx);
+      tz.push_back(az);
+      tx.push_back(ax);
+      az += h->plan[1].ntiles;
+      ax += h->plan[0].ntiles;
+      PrepParams<T> q{};
+      q.g = h->g;
+      for (int d = 0; d < 3; d++) q.n[d] = h->n[d];
+      for (int d = 0; d < h->ndim; d++) q.tab[d] = tb[d];
+      q.pot = h->dpot;
+      q.ctrl = h->ctrl;
+      pp.push_back(q);
+      b->smem2d = std::max(b->smem2d, std::max(h->plan[0].smem, h->plan[1].smem));
+    }
+    b->ntiles_z = az;
+    b->ntiles_x = ax;
+    WP_CUDA(nullptr, cudaMalloc(&b->d_pass_z, pz.size() * sizeof(PassParams<T>)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_pass_x, px.size() * sizeof(PassParams<T>)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_prep, pp.size() * sizeof(PrepParams<T>)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_tiles_z, tz.size() * sizeof(int64_t)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_tiles_x, tx.size() * sizeof(int64_t)));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_pass_z, pz.data(), pz.size() * sizeof(PassParams<T>), cudaMemcpyHostToDevice));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_pass_x, px.data(), px.size() * sizeof(PassParams<T>), cudaMemcpyHostToDevice));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_prep, pp.data(), pp.size() * sizeof(PrepParams<T>), cudaMemcpyHostToDevice));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_z, tz.data(), tz.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_x, tx.data(), tx.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  b->dirty = false;
+  return WP_OK;
+}
+
+// The launches of one m-step chunk for every instance (capturable).
+template <class T>
+wp_status batch_issue(wp_batch* b, int64_t m) {
+  cudaStream_t st = b->stream;
+  const int n2 = (int)b->idx2d.size();
+  auto prep = [&](int add, double shift, double tau) -> wp_status {
+    b->launches++;
+    return launch_rc(nullptr, launch_prep_batch<T>((const PrepParams<T>*)b->d_prep, n2, add, shift, tau, st),
+                     "batched prep");
+  };
+  auto zpass = [&](uint32_t f) -> wp_status {
+    b->launches++;
+    return launch_rc(nullptr,
+                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, n2, b->ntiles_z, f, 0,
+                                          b->smem2d, st),
+                     "batched pass");
+  };
+  auto xpass = [&](int khalf) -> wp_status {
+    b->launches++;
+    return launch_rc(nullptr,
+                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, n2, b->ntiles_x, F_KIN,
+                                          khalf, b->smem2d, st),
+                     "batched pass");
+  };
+  wp_status s2;
+  for (auto& c : b->classes1d) {
+    b->launches++;
+    s2 = launch_rc(nullptr,
+                   launch_res1d_batch<T>((const Res1dParams<T>*)c.dparams, (int)c.idx.size(), c.nthreads, c.ept, m,
+                                         c.smem, st),
+                   "batched 1-D kernel");
+    if (s2 != WP_OK) return s2;
+  }
+  if (n2 > 0) {
+    if (b->order2d == WP_ORDER_VKV) {
+      if ((s2 = prep(0, 0.0, 0.5)) != WP_OK || (s2 = zpass(F_PHASE | F_FFT)) != WP_OK || (s2 = xpass(0)) != WP_OK)
+        return s2;
+      for (int64_t k = 1; k < m; k++)
+        if ((s2 = prep(1, 0.0, 1.0)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE | F_FFT)) != WP_OK ||
+            (s2 = xpass(0)) != WP_OK)
+          return s2;
+      if ((s2 = prep(1, 0.0, 0.5)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE)) != WP_OK) return s2;
+    } else {
+      if ((s2 = zpass(F_FFT)) != WP_OK || (s2 = xpass(1)) != WP_OK) return s2;
+      for (int64_t k = 0; k < m; k++)
+        if ((s2 = prep(k == 0 ? 0 : 1, 0.5, 1.0)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE | F_FFT)) != WP_OK ||
+            (s2 = xpass(k == m - 1 ? 1 : 0)) != WP_OK)
+          return s2;
+      if ((s2 = prep(1, 0.0, 0.0)) != WP_OK || (s2 = zpass(F_IFFT)) != WP_OK) return s2;
+    }
+  }
+  for (int k : b->idx_other) {
+    wp_handle* h = b->inst[k];
+    const int64_t save = h->host_step;
+    if ((s2 = chunk_seq<T>(h, m, false)) != WP_OK) return s2;
+    h->host_step = save;  // advanced uniformly below
+  }
+  return WP_OK;
+}
+
+template <class T>
+wp_status batch_step(wp_batch* b, int64_t m, bool use_graph) {
+  wp_status st;
+  if (b->dirty)
+    if ((st = batch_compile<T>(b)) != WP_OK) return bfail(b, st, g_err);
+  if (m <= 0) return WP_OK;
+  if (use_graph && b->seen[m] > 0) {
+    auto it = b->graphs.find(m);
+    if (it == b->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bfail(b, WP_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+      st = batch_issue<T>(b, m);
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (st != WP_OK) return bfail(b, st, g_err);
+      if (e != cudaSuccess) return bfail(b, WP_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+      cudaGraphExec_t ex = nullptr;
+      e = cudaGraphInstantiate(&ex, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(b, WP_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+      it = b->graphs.emplace(m, ex).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, b->stream);
+    if (e != cudaSuccess) return bfail(b, WP_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  } else {
+    if ((st = batch_issue<T>(b, m)) != WP_OK) return bfail(b, st, g_err);
+    b->seen[m]++;
+  }
+  for (wp_handle* h : b->inst) h->host_step += m;
+  return WP_OK;
+}
+
+}  // namespace
+
 // =================================================================== C ABI
 extern "C" {
 
@@ -997,7 +1257,7 @@ int64_t wp_get_step_index(const wp_handle* h) { return h ? h->host_step : 0; }
 wp_status wp_set_step_index(wp_handle* h, int64_t s) {
   if (!h) return fail(h, WP_EINVAL, "NULL handle");
   h->host_step = s;
-  return WP_OK;
+  return run_set_step(h, s);
 }
 
 int64_t wp_launch_count(const wp_handle* h) { return h ? h->launches : 0; }
@@ -1026,5 +1286,83 @@ wp_status wp_profile_read(wp_handle* h, int kernel, int64_t* launches, double* t
   h->prof_ms[kernel] = 0.0;
   return WP_OK;
 }
+
+
+wp_status wp_batch_create(int32_t precision, void* stream, wp_batch** out) {
+  if (!out) return fail(nullptr, WP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (precision != WP_C128 && precision != WP_C64 && precision != WP_C128_F32X2)
+    return fail(nullptr, WP_EINVAL, "unknown precision");
+  wp_batch* b = new (std::nothrow) wp_batch();
+  if (!b) return fail(nullptr, WP_ENOMEM, "host allocation failed");
+  b->prec = precision;
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return cuda_fail(nullptr, e, "stream creation");
+    }
+    b->own_stream = true;
+  }
+  *out = b;
+  return WP_OK;
+}
+
+wp_status wp_batch_add(wp_batch* b, const wp_problem* pb, const wp_potential* pot, int64_t* index) {
+  if (!b || !pb) return fail(nullptr, WP_EINVAL, "NULL argument");
+  if (pb->precision != b->prec) return bfail(b, WP_EINVAL, "instance precision differs from the batch");
+  wp_handle* h = nullptr;
+  wp_status st = wp_create(pb, b->stream, &h);
+  if (st != WP_OK) return bfail(b, st, g_err);
+  if (pot) {
+    st = wp_set_potential(h, pot);
+    if (st != WP_OK) {
+      b->err = h->err;
+      wp_destroy(h);
+      return st;
+    }
+  }
+  b->inst.push_back(h);
+  b->dirty = true;
+  if (index) *index = (int64_t)b->inst.size() - 1;
+  return WP_OK;
+}
+
+wp_handle* wp_batch_handle(wp_batch* b, int64_t index) {
+  if (!b || index < 0 || index >= (int64_t)b->inst.size()) return nullptr;
+  return b->inst[index];
+}
+
+int64_t wp_batch_size(const wp_batch* b) { return b ? (int64_t)b->inst.size() : 0; }
+
+wp_status wp_batch_step(wp_batch* b, int64_t nsteps, int use_graph) {
+  if (!b) return fail(nullptr, WP_EINVAL, "NULL batch");
+  if (nsteps < 0) return bfail(b, WP_EINVAL, "nsteps < 0");
+  if (b->inst.empty()) return WP_OK;
+  if (b->prec == WP_C64) return batch_step<float>(b, nsteps, use_graph != 0);
+  if (b->prec == WP_C128_F32X2) return batch_step<ff>(b, nsteps, use_graph != 0);
+  return batch_step<double>(b, nsteps, use_graph != 0);
+}
+
+int64_t wp_batch_launch_count(const wp_batch* b) {
+  if (!b) return 0;
+  int64_t n = b->launches;
+  for (const wp_handle* h : b->inst) n += h->launches;
+  return n;
+}
+
+wp_status wp_batch_destroy(wp_batch* b) {
+  if (!b) return WP_OK;
+  cudaStreamSynchronize(b->stream);
+  batch_free_compiled(b);
+  for (wp_handle* h : b->inst) wp_destroy(h);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return WP_OK;
+}
+
+const char* wp_batch_last_error(const wp_batch* b) { return b ? b->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"

@@ -176,6 +176,8 @@ struct PassParams {
   double* partials;    // [gridDim.x][NQ]
   const TwE<T>* Prec;      // pass-axis potential-phase records
   const TwE<T>* Krec;      // pass-axis kinetic records
+  const cx<T>* Khalf_axes[3];     // dt/2 kinetic factors (batched kinetic pass, KVK ends)
+  const cx<T>* Khalf_lo_axes[3];
   const LineRec<T>* lines_phase;
   const LineRec<T>* lines_kin;
 };
@@ -267,6 +269,13 @@ template <class T> int launch_res1d(const Res1dParams<T>& p, size_t smem, void* 
 template <class T> int launch_convert(const ConvParams<T>& p, void* stream);
 template <class T> int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream);
 template <class T> int launch_lines(const LinesParams<T>& p, void* stream);
+// batched launches (one block range per instance)
+template <class T> int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, int ninst,
+                                         int64_t ntiles, uint32_t flags, int khalf, size_t smem, void* stream);
+template <class T> int launch_prep_batch(const PrepParams<T>* params, int ninst, int step_add, double shift_dt,
+                                         double tau_dt, void* stream);
+template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept,
+                                          int64_t nsteps, size_t smem, void* stream);
 int launch_reduce(const ReduceParams& p, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);

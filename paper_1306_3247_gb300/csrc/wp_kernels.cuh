@@ -596,8 +596,35 @@ __device__ __forceinline__ void tile_fft(cx<T>* s, const PassParams<T>& p, const
   fft_fixed<T, SH::logn, SH::logC, SH::LS, INV, 0>(s, reinterpret_cast<const TwE<T>*>(p.Wst), tid);
 }
 
+// Global line coordinates of tile `tile`: contiguous axis -> lines o0 .. o0 + C - 1;
+// strided axis -> outer index o0, columns cb .. cb + C - 1.
+template <class T, class SH>
+__device__ __forceinline__ void tile_origin(const PassParams<T>& p, const SH& sh, int64_t tile, int64_t& o0,
+                                            int64_t& cb) {
+  if (sh.contig) {
+    o0 = tile << sh.logC;
+    cb = 0;
+  } else {
+    const int tpo = p.log_inner - sh.logC;
+    o0 = tile >> tpo;
+    cb = (tile & ((int64_t(1) << tpo) - 1)) << sh.logC;
+  }
+}
+
+// Element (i, l) of the tile <-> global index. Loads and stores run with the lines
+// fastest: a warp touches 32 / C consecutive points of each of C lines (contiguous axis:
+// C full sectors; strided axis: one row segment of C adjacent columns) and consecutive
+// shared-memory words.
+template <class T, class SH>
+__device__ __forceinline__ int64_t tile_gidx(const PassParams<T>& p, const SH& sh, int64_t o0, int64_t cb, int i,
+                                             int l) {
+  return sh.contig ? ((o0 + l) << sh.logn) + i : (((o0 << sh.logn) + i) << p.log_inner) + cb + l;
+}
+
+// Everything a pass does once its tile is in shared memory: the transforms and factors
+// selected by the flags, the store, the partial sums. Ends with a block barrier.
 template <class T, int E, bool OBS, class SH>
-__device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, cx<T>* s) {
+__device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& sh, cx<T>* s, int64_t tile) {
   __shared__ double red[32][NQ];
   __shared__ double tot[NQ];
   __shared__ cx<T> sLh[64], sLl[64];
@@ -606,29 +633,11 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
   const int tid = threadIdx.x;
   const int nthr = sh.nthr;
   const int logn = sh.logn, logC = sh.logC, LS = sh.LS;
-  const int n = 1 << logn, C = 1 << logC;
-  const int64_t tile = blockIdx.x;
+  const int C = 1 << logC;
   const bool contig = sh.contig;
   int64_t o0, cb;
-  if (contig) {
-    o0 = tile << logC;
-    cb = 0;
-  } else {
-    const int tpo = p.log_inner - logC;
-    o0 = tile >> tpo;
-    cb = (tile & ((int64_t(1) << tpo) - 1)) << logC;
-  }
+  tile_origin(p, sh, tile, o0, cb);
   const int ntot = C << logn;
-
-  // load the tile with the lines fastest: a warp reads 32 / C consecutive points of each
-  // of C lines (contiguous axis: C separate full sectors; strided axis: one row segment
-  // of C adjacent columns), and writes consecutive shared-memory words
-  for (int e = tid; e < ntot; e += nthr) {
-    const int i = e >> logC, l = e & (C - 1);
-    const int64_t gidx = contig ? ((o0 + l) << logn) + i : (((o0 << logn) + i) << p.log_inner) + cb + l;
-    s[i * LS + l] = p.in[gidx];
-  }
-  __syncthreads();
 
   const uint32_t f = p.flags;
   if (f & F_IFFT) tile_fft<T, E, true>(s, p, sh, tid);
@@ -684,12 +693,7 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
         }
         acc[Q_V] += V * rho;
         if (f & F_AUTOCORR) {
-          int64_t gidx;
-          if (contig)
-            gidx = ((o0 + l) << logn) + i;
-          else
-            gidx = (((o0 << logn) + i) << p.log_inner) + cb + l;
-          const cx<T> z = p.psi0[gidx];
+          const cx<T> z = p.psi0[tile_gidx(p, sh, o0, cb, i, l)];
           acc[Q_AC_RE] += (double)z.re * re + (double)z.im * im;
           acc[Q_AC_IM] += (double)z.re * im - (double)z.im * re;
         }
@@ -743,8 +747,7 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
   if (!(f & F_NO_STORE)) {
     for (int e = tid; e < ntot; e += nthr) {
       const int i = e >> logC, l = e & (C - 1);
-      const int64_t gidx = contig ? ((o0 + l) << logn) + i : (((o0 << logn) + i) << p.log_inner) + cb + l;
-      p.out[gidx] = s[i * LS + l];
+      p.out[tile_gidx(p, sh, o0, cb, i, l)] = s[i * LS + l];
     }
   }
 
@@ -752,6 +755,22 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
     block_sum(acc, tot, red);
     if (tid < NQ) p.partials[blockIdx.x * (int64_t)NQ + tid] = tot[tid];
   }
+  __syncthreads();
+}
+
+// One tile per block: synchronous load, then compute.
+template <class T, int E, bool OBS, class SH>
+__device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, cx<T>* s) {
+  const int64_t tile = blockIdx.x;
+  int64_t o0, cb;
+  tile_origin(p, sh, tile, o0, cb);
+  const int C = 1 << sh.logC, ntot = C << sh.logn;
+  for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
+    const int i = e >> sh.logC, l = e & (C - 1);
+    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
+  }
+  __syncthreads();
+  pass_compute<T, E, OBS>(p, sh, s, tile);
 }
 
 // E elements per thread; the block has at most 32 E threads, so a tile holds at most
@@ -760,6 +779,58 @@ template <class T, int E, bool OBS>
 __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pass_body<T, E, OBS>(p, DynShape(p), reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+// Batched pass over many instances: tile_start[k] is the first block of instance k (a
+// prefix sum of the instances' tile counts); every instance tiles its lines into
+// 2048-element tiles with 256 threads. The block finds its instance by binary search,
+// copies that instance's parameters to shared memory and runs the same pass body.
+template <class T>
+__global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
+                                                    const int64_t* __restrict__ tile_start, int ninst,
+                                                    uint32_t flags, int khalf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
+  __shared__ int s_inst;
+  PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
+  if (threadIdx.x == 0) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tile_start[mid] <= (int64_t)blockIdx.x)
+        lo = mid;
+      else
+        hi = mid - 1;
+    }
+    s_inst = lo;
+  }
+  __syncthreads();
+  const int inst = s_inst;
+  const int* src = reinterpret_cast<const int*>(&params[inst]);
+  for (int k = threadIdx.x; k < (int)(sizeof(PassParams<T>) / sizeof(int)); k += blockDim.x)
+    reinterpret_cast<int*>(raw)[k] = src[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.flags = flags;
+    if (khalf)
+      for (int d = 0; d < 3; d++) {
+        p.K[d] = p.Khalf_axes[d];
+        p.K_lo[d] = p.Khalf_lo_axes[d];
+      }
+  }
+  __syncthreads();
+  const int64_t tile = (int64_t)blockIdx.x - tile_start[inst];
+  const DynShape sh(p);
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  int64_t o0, cb;
+  tile_origin(p, sh, tile, o0, cb);
+  const int C = 1 << sh.logC, ntot = C << sh.logn;
+  for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
+    const int i = e >> sh.logC, l = e & (C - 1);
+    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
+  }
+  __syncthreads();
+  pass_compute<T, 8, false>(p, sh, s, tile);
 }
 
 // Fixed-size pass: n = 2^LOGN points per line, 2048-element tiles, 256 threads.
@@ -813,7 +884,7 @@ __global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
 // exp(-i A_d tau/hbar) (argument reduced by the FP64 sincos), and the Gaussian-term
 // factors; the Gaussian coefficients f_g(t) and f_g(t) tau/hbar go to the control block.
 template <class T>
-__global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
+__device__ void prep_body(const PrepParams<T>& p) {
   __shared__ int64_t s_step;
   if (threadIdx.x == 0) s_step = p.ctrl->step + p.step_add;
   __syncthreads();
@@ -858,6 +929,31 @@ __global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
   if (threadIdx.x == 0) p.ctrl->step = step;
 }
 
+template <class T>
+__global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
+  prep_body<T>(p);
+}
+
+// Batched tables: block b updates instance b. The step increment, the time shift and the
+// phase length (in units of the instance's dt) are the same for all instances.
+template <class T>
+__global__ void __launch_bounds__(256) k_prep_batch(const PrepParams<T>* __restrict__ params, int step_add,
+                                                    double shift_dt, double tau_dt) {
+  __shared__ __align__(16) unsigned char raw[sizeof(PrepParams<T>)];
+  PrepParams<T>& p = *reinterpret_cast<PrepParams<T>*>(raw);
+  const int* src = reinterpret_cast<const int*>(&params[blockIdx.x]);
+  for (int k = threadIdx.x; k < (int)(sizeof(PrepParams<T>) / sizeof(int)); k += blockDim.x)
+    reinterpret_cast<int*>(raw)[k] = src[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.step_add = step_add;
+    p.t_shift = shift_dt * p.g.dt;
+    p.tau = tau_dt * p.g.dt;
+  }
+  __syncthreads();
+  prep_body<T>(p);
+}
+
 // ------------------------------------------------------------------ 1-D resident kernel
 // One CTA holds one 1-D line in shared memory for a chunk of steps: the whole step
 // (potential phase, FFT, kinetic factor, inverse FFT) runs without touching HBM.
@@ -897,13 +993,11 @@ __device__ void res1d_kinetic(cx<T>* s, const Res1dParams<T>& p, const cx<T>* K,
   fft_tile<T, E, true>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
 }
 
-template <class T, int E, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_res1d(const Res1dParams<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <class T, int E>
+__device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
   __shared__ double red[32][NQ];
   __shared__ double qp[NQ], qm[NQ];
   __shared__ double fco[WP_MAX_TERMS];
-  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int tid = threadIdx.x, nthr = p.nthreads;
   const int n = 1 << p.logn;
   const int64_t s0 = p.ctrl->step;
@@ -985,6 +1079,30 @@ __global__ void __launch_bounds__(MAXT) k_res1d(const Res1dParams<T> p) {
     }
   }
   if (tid == 0) p.ctrl->step = s0 + m;
+}
+
+template <class T, int E, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_res1d(const Res1dParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  res1d_body<T, E>(p, reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+// Batched resident lines: block b runs instance b (all of one line length) for nsteps.
+template <class T, int E, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_res1d_batch(const Res1dParams<T>* __restrict__ params, int64_t nsteps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) unsigned char raw[sizeof(Res1dParams<T>)];
+  Res1dParams<T>& p = *reinterpret_cast<Res1dParams<T>*>(raw);
+  const int* src = reinterpret_cast<const int*>(&params[blockIdx.x]);
+  for (int k = threadIdx.x; k < (int)(sizeof(Res1dParams<T>) / sizeof(int)); k += blockDim.x)
+    reinterpret_cast<int*>(raw)[k] = src[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    p.nsteps = nsteps;
+    p.obs = 0;
+  }
+  __syncthreads();
+  res1d_body<T, E>(p, reinterpret_cast<cx<T>*>(smem_raw));
 }
 
 #ifdef WP_COMMON_KERNELS

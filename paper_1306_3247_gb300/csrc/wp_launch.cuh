@@ -100,6 +100,50 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
   return cuda_status(cudaGetLastError());
 }
 
+template <class T>
+int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, int ninst, int64_t ntiles,
+                      uint32_t flags, int khalf, size_t smem, void* stream) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_pass_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    attr = true;
+  }
+  if (ntiles > 0)
+    k_pass_batch<T><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, ninst, flags, khalf);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_prep_batch(const PrepParams<T>* params, int ninst, int step_add, double shift_dt, double tau_dt,
+                      void* stream) {
+  if (ninst > 0)
+    k_prep_batch<T><<<(unsigned)ninst, 256, 0, (cudaStream_t)stream>>>(params, step_add, shift_dt, tau_dt);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept, int64_t nsteps, size_t smem,
+                       void* stream) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_res1d_batch<T, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_res1d_batch<T, 16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_res1d_batch<T, 16, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  if (ninst <= 0) return 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ept == 8 && nthreads <= 256)
+    k_res1d_batch<T, 8, 256><<<(unsigned)ninst, nthreads, smem, st>>>(params, nsteps);
+  else if (ept == 16 && nthreads <= 512)
+    k_res1d_batch<T, 16, 512><<<(unsigned)ninst, nthreads, smem, st>>>(params, nsteps);
+  else if (ept == 16 && nthreads <= 1024)
+    k_res1d_batch<T, 16, 1024><<<(unsigned)ninst, nthreads, smem, st>>>(params, nsteps);
+  else
+    return (int)cudaErrorInvalidConfiguration;
+  return cuda_status(cudaGetLastError());
+}
+
 #define WP_INSTANTIATE(T)                                                         \
   template int pass_smem_limit_set<T>(size_t);                                    \
   template int res1d_smem_limit_set<T>(size_t);                                   \
@@ -108,6 +152,10 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
   template int launch_res1d<T>(const Res1dParams<T>&, size_t, void*);            \
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
   template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
-  template int launch_lines<T>(const LinesParams<T>&, void*);
+  template int launch_lines<T>(const LinesParams<T>&, void*);                    \
+  template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, int, int64_t, uint32_t, int, size_t,  \
+                                    void*);                                      \
+  template int launch_prep_batch<T>(const PrepParams<T>*, int, int, double, double, void*);                    \
+  template int launch_res1d_batch<T>(const Res1dParams<T>*, int, int, int, int64_t, size_t, void*);
 
 }  // namespace wp

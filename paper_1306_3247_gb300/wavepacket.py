@@ -105,6 +105,14 @@ def load_library(build_if_missing: bool = True):
         "wp_destroy": ([H], ctypes.c_int),
         "wp_last_error": ([H], ctypes.c_char_p),
         "wp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "wp_batch_create": ([ctypes.c_int32, vp, P(vp)], ctypes.c_int),
+        "wp_batch_add": ([vp, P(WpProblem), P(WpPotential), P(ctypes.c_int64)], ctypes.c_int),
+        "wp_batch_handle": ([vp, ctypes.c_int64], vp),
+        "wp_batch_size": ([vp], ctypes.c_int64),
+        "wp_batch_step": ([vp, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
+        "wp_batch_launch_count": ([vp], ctypes.c_int64),
+        "wp_batch_destroy": ([vp], ctypes.c_int),
+        "wp_batch_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -365,6 +373,76 @@ class Propagator:
     def profile_read(self):
         names = wp_kernel_names()
         return {nm: wp_profile_read(self.h, i) for i, nm in enumerate(names)}
+
+
+class Batch:
+    """Many independent propagations advanced together (wp_batch_*)."""
+
+    def __init__(self, precision="c128", stream=None):
+        lib = load_library()
+        self.lib = lib
+        self.precision = precision
+        h = ctypes.c_void_p()
+        st = lib.wp_batch_create(PRECISIONS[precision], ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        _check(lib, None, st)
+        self.b = h
+        self.shapes = []
+        self.problems = []
+
+    def add(self, problem: dict, terms=(), autocorr=False) -> int:
+        pb = make_problem(problem, self.precision, autocorr)
+        pot = make_potential(list(terms))
+        idx = ctypes.c_int64(-1)
+        st = self.lib.wp_batch_add(self.b, ctypes.byref(pb), ctypes.byref(pot), ctypes.byref(idx))
+        if st != WP_OK:
+            raise WavepacketError(st, self.lib.wp_batch_last_error(self.b).decode(errors="replace"))
+        self.shapes.append(tuple(int(x) for x in problem["n"][: int(problem["ndim"])]))
+        self.problems.append(pb)
+        return idx.value
+
+    def handle(self, k: int):
+        return ctypes.c_void_p(self.lib.wp_batch_handle(self.b, int(k)))
+
+    def init_gaussian(self, k, x0, p0, sigma):
+        wp_init_gaussian(self.handle(k), x0, p0, sigma)
+
+    def set_state(self, k, psi):
+        a = np.ascontiguousarray(psi, dtype=np.complex128).reshape(self.shapes[k])
+        wp_set_state(self.handle(k), a.ctypes.data, False)
+
+    def get_state(self, k) -> np.ndarray:
+        out = np.empty(self.shapes[k], dtype=np.complex128)
+        wp_get_state(self.handle(k), out.ctypes.data, False)
+        return out
+
+    def step(self, nsteps: int, use_graph: bool = True):
+        st = self.lib.wp_batch_step(self.b, int(nsteps), 1 if use_graph else 0)
+        if st != WP_OK:
+            raise WavepacketError(st, self.lib.wp_batch_last_error(self.b).decode(errors="replace"))
+
+    @property
+    def launches(self) -> int:
+        return self.lib.wp_batch_launch_count(self.b)
+
+    def __len__(self):
+        return self.lib.wp_batch_size(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.wp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def problem_points(problem: dict) -> int:
