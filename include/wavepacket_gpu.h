@@ -198,6 +198,31 @@ int64_t wp_batch_launch_count(const wp_batch* b);  /* kernel launches issued (gr
 wp_status wp_batch_destroy(wp_batch* b);
 const char* wp_batch_last_error(const wp_batch* b);
 
+/* Serving: a continuous-batching request loop. Requests (a problem, its potential, the
+ * Sec. 4.2 Gaussian packet parameters and a step count) queue in arrival order.
+ * wp_server_progress (non-blocking) admits queued requests while a stream slot is free
+ * and the estimated device bytes of the running requests stay within budget_bytes,
+ * issues the next chunk of at most chunk_steps steps for every running request whose
+ * previous chunk completed, and writes the ids of requests that finished since the last
+ * call to done_ids (up to cap; *ndone gets the count). Each running request owns one of
+ * nslots streams, so kernels of different requests overlap on the device; a request's
+ * result is the one its handle gives alone. wp_server_fetch copies a finished request's
+ * state (complex128, host, may be NULL) and final observables (may be NULL), returns
+ * its submit / admit / finish times (seconds, steady clock, may be NULL) and releases
+ * it. Errors: WP_EINVAL, WP_ENOMEM (a request above the budget), WP_EBUSY (fetch of an
+ * unfinished request), WP_ECUDA; message in wp_server_last_error. */
+typedef struct wp_server wp_server;
+wp_status wp_server_create(int64_t budget_bytes, int32_t nslots, int64_t chunk_steps, wp_server** out);
+wp_status wp_server_submit(wp_server* s, int64_t id, const wp_problem* problem, const wp_potential* pot,
+                           const double x0[3], const double p0[3], const double sigma[3], int64_t nt);
+wp_status wp_server_progress(wp_server* s, int64_t* done_ids, int64_t cap, int64_t* ndone);
+wp_status wp_server_fetch(wp_server* s, int64_t id, void* psi_host, wp_obs* obs, double* times);
+int64_t wp_server_pending(const wp_server* s);     /* queued + running + finished, not fetched */
+int64_t wp_server_bytes_in_use(const wp_server* s);
+int32_t wp_server_running(const wp_server* s);
+wp_status wp_server_destroy(wp_server* s);
+const char* wp_server_last_error(const wp_server* s);
+
 /* Allocation-free moments. The paper has no counterpart of this call: it exists for
  * callers that cannot call cudaMalloc (a host application whose device memory is held
  * by its own pool or reserved up front, code in a callback where allocation is not

@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libwavepacket_gpu.so")
 SOURCES = ["wp_api.cu", "wp_kernels_f64.cu", "wp_kernels_f32.cu", "wp_kernels_ff.cu", "wp_fixed_f64.cu",
-           "wp_fixed_f32.cu", "wp_fixed_ff.cu", "wp_noalloc.cu"]
+           "wp_fixed_f32.cu", "wp_fixed_ff.cu", "wp_noalloc.cu", "wp_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

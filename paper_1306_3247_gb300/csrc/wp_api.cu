@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -206,6 +207,25 @@ void host_kinetic(const wp_handle* h, int d, double tau, double scale, std::vect
     re[j] = (double)(cosl(th) * (long double)scale);
     im[j] = (double)(sinl(th) * (long double)scale);
   }
+}
+
+// cudaFuncSetAttribute is global to a kernel, not to a handle: handles of different sizes
+// must never lower a limit another handle relies on. So every kernel gets the device's
+// opt-in maximum once per process and precision.
+template <class T>
+int ensure_smem_limits() {
+  static std::once_flag once;
+  static int rc = 0;
+  std::call_once(once, [] {
+    int dev = 0, mx = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || mx <= 0)
+      mx = 48 * 1024;
+    const size_t lim = (size_t)mx - 16 * 1024;  // room for the kernels' static shared memory
+    rc = pass_smem_limit_set<T>(lim);
+    if (!rc) rc = res1d_smem_limit_set<T>(lim);
+  });
+  return rc;
 }
 
 template <class T>
@@ -1107,7 +1127,8 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
       if ((st = WP_DISPATCH(h, run_lines<T>(h, false, k))) != WP_OK) return bail(st);
     size_t mx = 0;
     for (int d = 0; d < h->ndim; d++) mx = std::max(mx, h->plan[d].smem);
-    const int rc = WP_DISPATCH(h, pass_smem_limit_set<T>(mx));
+    const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
+    if (mx > 180 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "tile exceeds shared memory"));
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     if ((e = cudaMalloc(&h->part_pos, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
       return bail(cuda_fail(h, e, "partials allocation"));
@@ -1122,11 +1143,10 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     if (h->res_nthreads > 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long"));
     h->res_smem = (size_t)n * h->elem;
     if (h->res_smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long for shared memory"));
-    const int rc = WP_DISPATCH(h, res1d_smem_limit_set<T>(h->res_smem));
+    const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     h->plan[0] = make_plan(h, 0);
-    const int rc2 = WP_DISPATCH(h, pass_smem_limit_set<T>(h->res_smem));
-    if (rc2) return bail(cuda_fail(h, (cudaError_t)rc2, "shared-memory limit"));
+
   }
   if ((st = ensure_obs(h, 64)) != WP_OK) return bail(st);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));

@@ -113,6 +113,16 @@ def load_library(build_if_missing: bool = True):
         "wp_batch_launch_count": ([vp], ctypes.c_int64),
         "wp_batch_destroy": ([vp], ctypes.c_int),
         "wp_batch_last_error": ([vp], ctypes.c_char_p),
+        "wp_server_create": ([ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, P(vp)], ctypes.c_int),
+        "wp_server_submit": ([vp, ctypes.c_int64, P(WpProblem), P(WpPotential), P(ctypes.c_double),
+                              P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int64], ctypes.c_int),
+        "wp_server_progress": ([vp, P(ctypes.c_int64), ctypes.c_int64, P(ctypes.c_int64)], ctypes.c_int),
+        "wp_server_fetch": ([vp, ctypes.c_int64, vp, P(WpObs), P(ctypes.c_double)], ctypes.c_int),
+        "wp_server_pending": ([vp], ctypes.c_int64),
+        "wp_server_bytes_in_use": ([vp], ctypes.c_int64),
+        "wp_server_running": ([vp], ctypes.c_int32),
+        "wp_server_destroy": ([vp], ctypes.c_int),
+        "wp_server_last_error": ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -431,6 +441,81 @@ class Batch:
         if getattr(self, "b", None):
             self.lib.wp_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request loop (wp_server_*)."""
+
+    def __init__(self, budget_bytes=80e9, nslots=32, chunk_steps=50):
+        lib = load_library()
+        self.lib = lib
+        h = ctypes.c_void_p()
+        st = lib.wp_server_create(int(budget_bytes), int(nslots), int(chunk_steps), ctypes.byref(h))
+        if st != WP_OK:
+            raise WavepacketError(st, "wp_server_create failed")
+        self.s = h
+        self.shapes = {}
+        self._done = (ctypes.c_int64 * 4096)()
+
+    def _err(self, st):
+        raise WavepacketError(st, self.lib.wp_server_last_error(self.s).decode(errors="replace"))
+
+    def submit(self, rid: int, problem: dict, terms, init: dict, nt: int, precision="c64"):
+        pb = make_problem(problem, precision)
+        pot = make_potential(list(terms))
+        st = self.lib.wp_server_submit(self.s, int(rid), ctypes.byref(pb), ctypes.byref(pot),
+                                       _vec3(init["x0"], 0.0), _vec3(init["p0"], 0.0), _vec3(init["sigma"], 1.0),
+                                       int(nt))
+        if st != WP_OK:
+            self._err(st)
+        self.shapes[int(rid)] = tuple(int(x) for x in problem["n"][: int(problem["ndim"])])
+
+    def progress(self):
+        n = ctypes.c_int64(0)
+        st = self.lib.wp_server_progress(self.s, self._done, len(self._done), ctypes.byref(n))
+        if st != WP_OK:
+            self._err(st)
+        return [self._done[k] for k in range(min(n.value, len(self._done)))]
+
+    def fetch(self, rid: int, want_state=False):
+        psi = np.empty(self.shapes[rid], dtype=np.complex128) if want_state else None
+        o = WpObs()
+        times = (ctypes.c_double * 3)()
+        st = self.lib.wp_server_fetch(self.s, int(rid), psi.ctypes.data if psi is not None else None,
+                                      ctypes.byref(o), times)
+        if st != WP_OK:
+            self._err(st)
+        del self.shapes[rid]
+        return psi, _obs_array(ctypes.addressof(o), 1)[0], tuple(times)
+
+    @property
+    def pending(self) -> int:
+        return self.lib.wp_server_pending(self.s)
+
+    @property
+    def running(self) -> int:
+        return self.lib.wp_server_running(self.s)
+
+    @property
+    def bytes_in_use(self) -> int:
+        return self.lib.wp_server_bytes_in_use(self.s)
+
+    def close(self):
+        if getattr(self, "s", None):
+            self.lib.wp_server_destroy(self.s)
+            self.s = None
 
     def __del__(self):
         try:

@@ -1,0 +1,58 @@
+"""Continuous-batching server: every request's result is the same alone and in the mix,
+admission respects the memory budget, and the latency bookkeeping is consistent."""
+import numpy as np
+import pytest
+
+from paper_1306_3247_gb300 import serving as S
+from paper_1306_3247_gb300 import wavepacket as WPK
+from paper_1306_3247_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def small_stream(count=14, seed=7):
+    out = []
+    for arr, job in W.request_stream(count=count, seed=seed):
+        pb = dict(job["problem"])
+        cap = {1: 4096, 2: 128, 3: 32}[pb["ndim"]]
+        pb["n"] = [min(x, cap) for x in pb["n"]]
+        nt = min(job["nt"], 120)
+        out.append((arr, dict(job, problem=pb, nt=nt, nprint=nt)))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_served_results_equal_alone(precision):
+    reqs = small_stream()
+    chunk = 25
+    summary, results = S.serve(reqs, budget_bytes=2e9, nslots=4, chunk_steps=chunk, precision=precision,
+                               time_scale=0.01, want_states=True)
+    assert summary["requests"] == len(reqs) and len(results) == len(reqs)
+    assert summary["p50_ms"] <= summary["p99_ms"]
+    for rid, (arr, job) in enumerate(reqs):
+        with WPK.Propagator(job["problem"], job["terms"], precision) as P:
+            P.init_gaussian(**job["init"])
+            left = job["nt"]
+            while left > 0:
+                m = min(chunk, left)
+                P.step(m)
+                left -= m
+            alone = P.get_state()
+            obs_alone = P.observe()
+        obs, psi, lat = results[rid]
+        assert np.array_equal(psi, alone), rid
+        assert obs["norm"] == obs_alone["norm"] and obs["step"] == job["nt"]
+        assert lat > 0
+
+
+def test_budget_limits_concurrency():
+    reqs = small_stream(count=8, seed=3)
+    one = max(W_bytes for W_bytes in [2 ** 22])
+    # a budget that fits only small requests one at a time still completes the stream
+    summary, results = S.serve(reqs, budget_bytes=64e6, nslots=8, chunk_steps=40, time_scale=0.0)
+    assert len(results) == len(reqs)
+    with WPK.Server(1e6, 2, 10) as srv:
+        big = W.config_3d_barrier(n=64)
+        with pytest.raises(WPK.WavepacketError) as e:
+            srv.submit(0, big["problem"], big["terms"], big["init"], 10)
+        assert e.value.status == WPK.WP_ENOMEM
