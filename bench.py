@@ -1,20 +1,28 @@
 """Benchmark of the split-operator propagation (arXiv:1306.3247) on GB300.
 
-One bench step = one complete propagation job of the 3-D workload: a Gaussian packet
-(sigma 1.5, p0 = (2,0,0), centred at (-3,0,0)) on a 256^3 grid over [-30,30)^3
-scattering off the time-dependent spherical barrier 1.5 (1 + 0.3 sin 2t) exp(-|r|^2),
-dt = 0.002, 200 Strang steps, observables (norm, <x>, <p>, <x^2>, energies) every 20
-steps. Metric: grid-point steps per second over all ranks.
+Headline (`value`): the plain FP64 form on the 3-D workload. One bench step = one
+complete propagation job: a Gaussian packet (sigma 1.5, p0 = (2,0,0), centred at
+(-3,0,0)) on a 256^3 grid over [-30,30)^3 scattering off the time-dependent spherical
+barrier 1.5 (1 + 0.3 sin 2t) exp(-|r|^2), dt = 0.002, 200 Strang steps, observables
+(norm, <x>, <p>, <x^2>, energies) every 20 steps. Metric: grid-point steps per second
+over all ranks.
 
-  value  -- device-resident input: the initial state already in HBM, the timed job
-            starts from a device-to-device copy of it.
-  e2e    -- the same job through the C ABI with host buffers: host-to-device copy of
-            psi(0) from pinned memory, the run, device-to-host copy of psi(T) and of
-            the observables, all inside the timed region.
+  value   -- device-resident input: the initial state already in HBM, each timed job
+             starts from a device-to-device copy of it.
+  e2e     -- the same job through the C ABI with host buffers: host-to-device copy of
+             psi(0) from pinned memory, the run, device-to-host copy of psi(T) and of the
+             observables, all inside the timed region.
+  forms   -- the same job in the float-float complex128-accuracy form and in complex64.
+  batched -- 4096 uneven 1-D/2-D driven-trap instances advanced together (complex64,
+             chunks of 20 steps replayed as CUDA graphs), next to the plain per-instance
+             FP64 form on a subset of the same instances.
+  served  -- a Poisson request stream (1-D/2-D/3-D jobs, complex64) through the
+             continuous-batching server under an 80 GB budget: p50/p99 latency, offered
+             and achieved rates.
 
 --impl reference times the FP64 CPU oracle (the checker) on a bounded sample of the
-same workload on the host cores. With --gpus N > 1 (torchrun) every rank runs an
-independent replica of the job ("replicas only": the method has no exchange step).
+3-D workload on the host cores. With --gpus N > 1 (torchrun) every rank runs an
+independent replica ("replicas only": the method has no exchange step).
 """
 import argparse
 import json
@@ -35,6 +43,7 @@ from paper_1306_3247_gb300 import workloads as W  # noqa: E402
 
 METRIC = "grid-point·steps/s (256³ c128 plain vs batched c64) + served p50/p99 ms"
 UNIT = "grid-point·steps/s"
+FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate measured on this machine's GB300 (profiles/gb300_alu_rates.md)
 
 
 def peaks():
@@ -46,7 +55,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled during a timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -84,9 +93,7 @@ class ClockSampler:
                 self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm = []
-        mx = []
-        reasons = set()
+        sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for s in self.samples:
             try:
@@ -143,25 +150,26 @@ def cpu_baseline_run(cfg, nsteps):
 
 
 def reference_arm(args, world, rank):
-    cfg = W.config_3d_barrier(n=256)
+    """The oracle, on the host cores, as the reference arm (rank 0 only)."""
     if rank != 0:
         return
     from oracle import oracle as O
+    cfg = W.config_3d_barrier(n=256)
     pb, terms = cfg["problem"], cfg["terms"]
     psi = O.gaussian(pb, **cfg["init"])
     npts = 256 ** 3
-    for _ in range(args.warmup):
-        psi = O.step(pb, terms, psi, 0)
+    for k in range(args.warmup):
+        psi = O.step(pb, terms, psi, k)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        psi = O.step(pb, terms, psi, k)
+        psi = O.step(pb, terms, psi, args.warmup + k)
     el = time.perf_counter() - t0
     v = npts * args.steps / el
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": cfg["name"] + " c128 VKV (oracle: 1 Strang step per bench step)",
+            "config": {"workload": cfg["name"] + " VKV (FP64 CPU oracle: one Strang step per bench step)",
                        "grid": [256, 256, 256], "dt": 0.002},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
                              "sample": "one Strang step of the 256^3 barrier workload per bench step"},
@@ -169,34 +177,21 @@ def reference_arm(args, world, rank):
     print(json.dumps(line))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c128f"])
-    ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--nt", type=int, default=200)
-    ap.add_argument("--cpu-steps", type=int, default=1)
-    ap.add_argument("--no-cpu", action="store_true")
-    args = ap.parse_args()
-    world, rank, local = dist_init(args)
-    if args.impl == "reference":
-        reference_arm(args, world, rank)
-        return
+def pass_flops_per_point(logn, kind):
+    """Algorithmic FLOPs per grid point of one pass: 5 log2 n per axis transform (the
+    standard radix-2 count) and 6 per complex multiply by a phase factor."""
+    fft = 5 * logn
+    return {"pass_contig": 2 * fft + 6, "pass_kinetic": 2 * fft + 6, "pass_strided": fft}.get(kind, fft)
 
+
+def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False):
     import torch
-    from paper_1306_3247_gb300 import wavepacket as WPK
-
-    torch.cuda.set_device(local)
     cfg = W.config_3d_barrier(n=args.n)
     pb, terms = cfg["problem"], cfg["terms"]
-    nt, nprint = args.nt, cfg["nprint"]
+    nprint = cfg["nprint"]
     npts = math.prod(pb["n"][: pb["ndim"]])
     stream = torch.cuda.Stream()
-    P = WPK.Propagator(pb, terms, args.precision, stream=stream.cuda_stream)
-    # resident initial state (complex128) and pinned host buffers
+    P = WPK.Propagator(pb, terms, precision, stream=stream.cuda_stream)
     P.init_gaussian(**cfg["init"])
     psi0_dev = torch.empty(P.shape, dtype=torch.complex128, device="cuda")
     P.get_state_device(psi0_dev)
@@ -217,78 +212,183 @@ def main():
         WPK.wp_get_state(P.h, host_out.data_ptr(), False)
         return obs
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         job_device()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks = ClockSampler(local) if with_clocks else None
+    if clocks:
+        clocks.start()
     barrier(world)
     torch.cuda.synchronize()
     launches0 = P.launches
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         obs = job_device()
     ev1.record(stream)
     torch.cuda.synchronize()
     dev_ms = ev0.elapsed_time(ev1)
     launches = P.launches - launches0
     barrier(world)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     dev_ms = max_over_ranks(world, dev_ms)
-    value = world * npts * nt * args.steps / (dev_ms / 1e3)
-
-    # end to end through the C ABI with host buffers
-    job_e2e()
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    out = {"value": world * npts * nt * steps / (dev_ms / 1e3), "ms_per_job": dev_ms / steps, "launches": launches,
+           "clocks": clk, "final_norm": float(obs["norm"][-1])}
+    if with_e2e:
         job_e2e()
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(world, time.perf_counter() - t0)
-    e2e = world * npts * nt * args.steps / e2e_s
-
-    # per-kernel durations with CUDA events on the launching stream (one extra job)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            job_e2e()
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks(world, time.perf_counter() - t0)
+        out["e2e"] = {"value": world * npts * nt * steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": npts * 16,
+                      "d2h_bytes_per_step": npts * 16 + 128 * (1 + nt // nprint)}
+    # per-kernel durations with CUDA events on the launching stream (one more job)
     P.profile(True)
     job_device()
     prof = P.profile_read()
     P.profile(False)
-    elem = 8 if args.precision == "c64" else 16
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dom_name, (dom_n, dom_ms) = dom
-    avg_s = dom_ms / max(1, dom_n) / 1e3
-    bytes_per_launch = 2 * npts * elem  # one read and one write of the state
-    achieved = bytes_per_launch / avg_s / 1e9
-    pk, src = peaks()
+    out["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in prof.items() if v[0]}
+    P.close()
+    return out
 
+
+def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset):
+    """The uneven-instance batch: all instances advance `chunk` steps per bench step."""
+    import torch
+    inst = W.batched_instances(count=count)
+    pts = [math.prod(c["problem"]["n"][: c["problem"]["ndim"]]) for c in inst]
+    B = WPK.Batch(precision)
+    for c in inst:
+        k = B.add(c["problem"], c["terms"])
+        B.init_gaussian(k, **c["init"])
+    for _ in range(warmup):
+        B.step(chunk, use_graph=True)
+    torch.cuda.synchronize()
+    l0 = B.launches
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        B.step(chunk, use_graph=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    launches = B.launches - l0
+    finite = bool(np.isfinite(B.get_state(0)).all())
+    B.close()
+    out = {"value": sum(pts) * chunk * steps / el, "instances": count, "points": int(sum(pts)),
+           "steps_per_bench_step": chunk, "ms_per_bench_step": el / steps * 1e3, "graph_launches_issued": launches,
+           "n1d": sum(1 for c in inst if c["problem"]["ndim"] == 1), "finite": finite, "precision": precision}
+    # plain per-instance FP64 form on a subset of the same instances, one handle at a time
+    sub = inst[:plain_subset]
+    handles = []
+    for c in sub:
+        P = WPK.Propagator(c["problem"], c["terms"], "c128")
+        P.init_gaussian(**c["init"])
+        P.step(chunk)
+        handles.append(P)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for P in handles:
+        P.step(chunk)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    for P in handles:
+        P.close()
+    out["plain_fp64_per_instance"] = {"value": sum(pts[:plain_subset]) * chunk / el, "instances": plain_subset}
+    return out
+
+
+def bench_served(WPK, nreq, precision):
+    from paper_1306_3247_gb300 import serving as S
+    reqs = W.request_stream()[:nreq]
+    summary, _ = S.serve(reqs, budget_bytes=80e9, nslots=32, chunk_steps=50, precision=precision)
+    summary["precision"] = precision
+    return summary
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c128f"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--nt", type=int, default=200)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="headline only (no forms, batch, serving)")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=120)
+    args = ap.parse_args()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+    from paper_1306_3247_gb300 import wavepacket as WPK
+
+    torch.cuda.set_device(local)
+    head = bench_3d(args, WPK, args.precision, world, local, args.steps, args.warmup, args.nt, with_e2e=True,
+                    with_clocks=True)
+    pk, src = peaks()
+    npts = args.n ** 3
+    logn = int(math.log2(args.n))
+    dom = max(head["kernels"].items(), key=lambda kv: kv[1]["launches"] * kv[1]["avg_ms"])
+    dom_name, dom_v = dom
+    avg_s = dom_v["avg_ms"] / 1e3
+    elem = 8 if args.precision == "c64" else 16
+    if args.precision == "c128":
+        flops = pass_flops_per_point(logn, dom_name) * npts
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA rate measured on the box (profiles/gb300_alu_rates.md)",
+                "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"],
+                "hbm_frac": 2 * npts * elem / avg_s / 1e9 / pk["hbm_gbs"]}
+    else:
+        achieved = 2 * npts * elem / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": src,
+                "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"]}
+    extra = {}
+    if not args.no_extra and rank == 0:
+        for form in ("c128f", "c64"):
+            if form == args.precision:
+                continue
+            r = bench_3d(args, WPK, form, 1, local, args.steps, 1, args.nt, with_e2e=False)
+            kd = max(r["kernels"].items(), key=lambda kv: kv[1]["launches"] * kv[1]["avg_ms"])
+            el = 8 if form == "c64" else 16
+            r["roofline"] = {"bound": "hbm", "kernel": kd[0],
+                             "achieved": 2 * npts * el / (kd[1]["avg_ms"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                             "unit": "GB/s"}
+            r["roofline"]["frac"] = r["roofline"]["achieved"] / pk["hbm_gbs"]
+            r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
+            extra.setdefault("forms", {})[form] = r
+        extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=3, warmup=3,
+                                         plain_subset=64)
+        extra["served"] = bench_served(WPK, args.serve_requests, "c64")
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, dt, cores = cpu_baseline_run(cfg, args.cpu_steps)
+        v, dt, cores = cpu_baseline_run(W.config_3d_barrier(n=args.n), args.cpu_steps)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{args.cpu_steps} Strang step(s) of the {args.n}^3 workload ({dt:.1f} s)"}
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {"c128": "f64", "c64": "f32", "c128f": "f32x2"}[args.precision],
+            "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_job"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128f": "f32x2"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": cfg["name"] + f" {args.precision} VKV, {nt} steps, observables every {nprint}",
-                       "grid": pb["n"], "dt": pb["dt"], "steps_per_job": nt, "parallelism": "replicas",
-                       "l2": "state 268 MB > 129 MB L2 (c128)"},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": npts * 16, "d2h_bytes_per_step": npts * 16
-                    + 16 * 8 * (1 + nt // nprint)},
-            "gpu_launches": int(launches),
-            "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk["hbm_gbs"],
-                         "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                         "peak_source": src, "avg_launch_ms": avg_s * 1e3, "launches": dom_n},
-            "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items() if v[0]},
-            "clocks": clk,
-            "cpu_baseline": cpu,
+            "config": {"workload": f"3d_barrier_{args.n}^3 {args.precision} VKV, {args.nt} steps per job, "
+                                   f"observables every 20",
+                       "grid": [args.n] * 3, "dt": 0.002, "steps_per_job": args.nt, "parallelism": "replicas",
+                       "l2": "state larger than the 129 MB L2 (268 MB complex128), no flush needed"},
+            "e2e": head["e2e"], "gpu_launches": int(head["launches"]), "roofline": roof,
+            "kernels": head["kernels"], "clocks": head["clocks"], "cpu_baseline": cpu,
         }
+        line.update(extra)
         print(json.dumps(line))
-    P.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -755,7 +755,8 @@ wp_status validate_problem(const wp_problem* pb) {
   for (int d = 0; d < pb->ndim; d++) {
     if (!is_pow2(pb->n[d]) || pb->n[d] < 2)
       return fail(nullptr, WP_EUNSUPPORTED, "every n[d] must be a power of two >= 2");
-    if (pb->n[d] > 8192) return fail(nullptr, WP_EUNSUPPORTED, "n[d] > 8192 is not supported");
+    const int64_t nmax = (pb->ndim == 1 && pb->precision == WP_C64) ? 16384 : 8192;
+    if (pb->n[d] > nmax) return fail(nullptr, WP_EUNSUPPORTED, "n[d] > 8192 (16384 for 1-D complex64) is not supported");
     if (!(pb->L[d] > 0.0) || !std::isfinite(pb->L[d]) || !std::isfinite(pb->xmin[d]))
       return fail(nullptr, WP_EINVAL, "L[d] must be finite and > 0");
   }

@@ -32,6 +32,7 @@ struct Job {
   int64_t bytes = 0;
   int slot = -1;
   JobState state = QUEUED;
+  wp_status failed = WP_OK;  // admission error, reported by wp_server_fetch
   wp_handle* h = nullptr;
   double t_submit = 0, t_admit = 0, t_done = 0;
 };
@@ -191,7 +192,23 @@ wp_status wp_server_progress(wp_server* s, int64_t* done_ids, int64_t cap, int64
     if (slot < 0) break;
     s->queue.pop_front();
     wp_status st = admit(s, j, slot);
-    if (st != WP_OK) return st;
+    if (st != WP_OK) {
+      // the request cannot run (e.g. an unsupported grid): finish it with its error
+      if (j.h) {
+        wp_destroy(j.h);
+        j.h = nullptr;
+      }
+      if (j.slot >= 0) {
+        s->slot_job[j.slot] = -1;
+        s->in_use -= j.bytes;
+        j.slot = -1;
+      }
+      j.failed = st;
+      j.state = DONE;
+      j.t_admit = j.t_done = now_s();
+      if (*ndone < cap && done_ids) done_ids[*ndone] = j.id;
+      (*ndone)++;
+    }
   }
   return WP_OK;
 }
@@ -202,6 +219,16 @@ wp_status wp_server_fetch(wp_server* s, int64_t id, void* psi_host, wp_obs* obs,
   if (it == s->jobs.end()) return sfail(s, WP_EINVAL, "unknown request id");
   Job& j = it->second;
   if (j.state != DONE) return sfail(s, WP_EBUSY, "request not finished");
+  if (j.failed != WP_OK) {
+    if (times) {
+      times[0] = j.t_submit;
+      times[1] = j.t_admit;
+      times[2] = j.t_done;
+    }
+    const wp_status f = j.failed;
+    s->jobs.erase(it);
+    return sfail(s, f, "request failed at admission");
+  }
   wp_status st = WP_OK;
   if (psi_host) st = wp_get_state(j.h, psi_host, 0);
   if (st == WP_OK && obs) st = wp_observe(j.h, obs);

@@ -20,6 +20,7 @@ def serve(requests, budget_bytes=80e9, nslots=32, chunk_steps=50, precision="c64
     per request id, (observables record, state or None, latency_s)."""
     results = {}
     lat = []
+    failed = []
     points_steps = 0
     with WPK.Server(budget_bytes, nslots, chunk_steps) as srv:
         t0 = time.perf_counter()
@@ -36,7 +37,11 @@ def serve(requests, budget_bytes=80e9, nslots=32, chunk_steps=50, precision="c64
             done = srv.progress()
             seen = time.perf_counter()
             for rid in done:
-                psi, obs, _ = srv.fetch(rid, want_states)
+                try:
+                    psi, obs, _ = srv.fetch(rid, want_states)
+                except WPK.WavepacketError as e:
+                    failed.append((rid, e.status))
+                    continue
                 job = requests[rid][1]
                 latency = seen - arrivals[rid]
                 lat.append(latency)
@@ -49,11 +54,13 @@ def serve(requests, budget_bytes=80e9, nslots=32, chunk_steps=50, precision="c64
     span = requests[-1][0] * time_scale if requests else 0.0
     summary = {
         "requests": n,
+        "completed": len(lat),
+        "failed": len(failed),
         "wall_s": wall,
         "offered_rate": n / span if span > 0 else None,
         "achieved_rate": n / wall if wall > 0 else None,
-        "p50_ms": float(np.percentile(lat_ms, 50)) if n else None,
-        "p99_ms": float(np.percentile(lat_ms, 99)) if n else None,
+        "p50_ms": float(np.percentile(lat_ms, 50)) if len(lat) else None,
+        "p99_ms": float(np.percentile(lat_ms, 99)) if len(lat) else None,
         "grid_point_steps_per_s": points_steps / wall if wall > 0 else None,
     }
     return summary, results

@@ -74,6 +74,20 @@ def test_1d_driven_trap_c128_1000_steps(order, prec):
     compare_obs(obs, ref_obs, 1e-10)
 
 
+def test_1d_longest_line_c64():
+    # 1-D complex64 lines go up to 16384 points (one resident block of 1024 threads)
+    pb = {"ndim": 1, "n": [16384], "xmin": [-40.0], "L": [80.0], "dt": 0.005, "t0": 0.0}
+    terms = [{"shape": "quad", "a": [0.25], "coef": {"A0": 1.0}},
+             {"shape": "linear", "a": [1.0], "coef": {"A": 0.1, "omega": 0.45}}]
+    psi0 = O.gaussian(pb, [1.0], [0.5], [1.5])
+    ref = O.propagate(pb, terms, psi0, 200)
+    with WPK.Propagator(pb, terms, "c64") as P:
+        P.set_state(psi0)
+        P.step(120)
+        P.step(80)
+        assert rel_l2(P.get_state(), ref) < TOL64
+
+
 def test_1d_driven_trap_c64_1000_steps():
     cfg = W.config_1d_driven_trap()
     pb, terms = cfg["problem"], cfg["terms"]
