@@ -154,10 +154,10 @@ def reference_arm(args, world, rank):
     if rank != 0:
         return
     from oracle import oracle as O
-    cfg = W.config_3d_barrier(n=256)
+    cfg = W.config_3d_barrier(n=args.grid)
     pb, terms = cfg["problem"], cfg["terms"]
     psi = O.gaussian(pb, **cfg["init"])
-    npts = 256 ** 3
+    npts = args.grid ** 3
     for k in range(args.warmup):
         psi = O.step(pb, terms, psi, k)
     t0 = time.perf_counter()
@@ -170,9 +170,9 @@ def reference_arm(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": cfg["name"] + " VKV (FP64 CPU oracle: one Strang step per bench step)",
-                       "grid": [256, 256, 256], "dt": 0.002},
+                       "grid": [args.grid] * 3, "dt": 0.002},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": "one Strang step of the 256^3 barrier workload per bench step"},
+                             "sample": f"one Strang step of the {args.grid}^3 barrier workload per bench step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -186,7 +186,7 @@ def pass_flops_per_point(logn, kind):
 
 def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False):
     import torch
-    cfg = W.config_3d_barrier(n=args.n)
+    cfg = W.config_3d_barrier(n=args.grid)
     pb, terms = cfg["problem"], cfg["terms"]
     nprint = cfg["nprint"]
     npts = math.prod(pb["n"][: pb["ndim"]])
@@ -314,7 +314,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c128f"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--grid", type=int, default=256, help="points per axis of the 3-D workload")
     ap.add_argument("--nt", type=int, default=200)
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
@@ -334,8 +334,8 @@ def main():
     head = bench_3d(args, WPK, args.precision, world, local, args.steps, args.warmup, args.nt, with_e2e=True,
                     with_clocks=True)
     pk, src = peaks()
-    npts = args.n ** 3
-    logn = int(math.log2(args.n))
+    npts = args.grid ** 3
+    logn = int(math.log2(args.grid))
     dom = max(head["kernels"].items(), key=lambda kv: kv[1]["launches"] * kv[1]["avg_ms"])
     dom_name, dom_v = dom
     avg_s = dom_v["avg_ms"] / 1e3
@@ -371,18 +371,18 @@ def main():
         extra["served"] = bench_served(WPK, args.serve_requests, "c64")
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, dt, cores = cpu_baseline_run(W.config_3d_barrier(n=args.n), args.cpu_steps)
+        v, dt, cores = cpu_baseline_run(W.config_3d_barrier(n=args.grid), args.cpu_steps)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{args.cpu_steps} Strang step(s) of the {args.n}^3 workload ({dt:.1f} s)"}
+               "sample": f"{args.cpu_steps} Strang step(s) of the {args.grid}^3 workload ({dt:.1f} s)"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_job"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": {"c128": "f64", "c64": "f32", "c128f": "f32x2"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": f"3d_barrier_{args.n}^3 {args.precision} VKV, {args.nt} steps per job, "
+            "config": {"workload": f"3d_barrier_{args.grid}^3 {args.precision} VKV, {args.nt} steps per job, "
                                    f"observables every 20",
-                       "grid": [args.n] * 3, "dt": 0.002, "steps_per_job": args.nt, "parallelism": "replicas",
+                       "grid": [args.grid] * 3, "dt": 0.002, "steps_per_job": args.nt, "parallelism": "replicas",
                        "l2": "state larger than the 129 MB L2 (268 MB complex128), no flush needed"},
             "e2e": head["e2e"], "gpu_launches": int(head["launches"]), "roofline": roof,
             "kernels": head["kernels"], "clocks": head["clocks"], "cpu_baseline": cpu,
