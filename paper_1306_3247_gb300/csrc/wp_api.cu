@@ -405,6 +405,31 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.Krec = khalf ? tb[axis].Khalf_rec : tb[axis].Kfull_rec;
   p.lines_phase = (const LineRec<T>*)h->lines_phase;
   p.lines_kin = (const LineRec<T>*)h->lines_kin[khalf ? 1 : 0];
+  p.Krec_half = tb[axis].Khalf_rec;
+  p.lines_kin_half = (const LineRec<T>*)h->lines_kin[1];
+  for (int d = 0; d < h->ndim; d++) {
+    p.Khalf_axes[d] = tb[d].Khalf;
+    p.Khalf_lo_axes[d] = tb[d].Khalf_lo;
+  }
+  return p;
+}
+
+template <class T>
+LinesParams<T> phase_lines_params(wp_handle* h) {
+  LinesParams<T> p{};
+  AxisTab<T>* tb = tabs<T>(h);
+  p.g = h->g;
+  p.axis = h->ndim - 1;
+  p.gauss = 1;
+  p.ngauss = h->hpot.ngauss;
+  p.nlines = h->nlines_phase;
+  for (int d = 0; d < h->ndim; d++) {
+    p.H[d] = tb[d].P;
+    p.Lo[d] = tb[d].P_lo;
+    for (int gg = 0; gg < WP_MAX_GAUSS; gg++) p.Gd[gg][d] = tb[d].Gd[gg];
+  }
+  p.ctrl = h->ctrl;
+  p.out = (LineRec<T>*)h->lines_phase;
   return p;
 }
 
@@ -794,8 +819,14 @@ struct wp_batch {
   void* d_pass_z = nullptr;
   void* d_pass_x = nullptr;
   void* d_prep = nullptr;
+  void* d_lines = nullptr;
+  int64_t max_lines = 0;
   int64_t* d_tiles_z = nullptr;
   int64_t* d_tiles_x = nullptr;
+  int* d_binst_z = nullptr;   // instance of every block of the batched passes
+  int* d_binst_x = nullptr;
+  cudaStream_t side = nullptr;  // second stream: the 1-D part runs beside the 2-D part
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t ntiles_z = 0, ntiles_x = 0;
   size_t smem2d = 0;
   std::map<int64_t, cudaGraphExec_t> graphs;
@@ -815,10 +846,13 @@ void batch_free_compiled(wp_batch* b) {
   for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
   b->graphs.clear();
   b->seen.clear();
-  void* ps[] = {b->d_pass_z, b->d_pass_x, b->d_prep, b->d_tiles_z, b->d_tiles_x};
+  void* ps[] = {b->d_pass_z, b->d_pass_x, b->d_prep, b->d_lines, b->d_tiles_z, b->d_tiles_x, b->d_binst_z,
+                b->d_binst_x};
   for (void* q : ps)
     if (q) cudaFree(q);
-  b->d_pass_z = b->d_pass_x = b->d_prep = nullptr;
+  b->d_pass_z = b->d_pass_x = b->d_prep = b->d_lines = nullptr;
+  b->d_binst_z = b->d_binst_x = nullptr;
+  b->max_lines = 0;
   b->d_tiles_z = b->d_tiles_x = nullptr;
   for (auto& c : b->classes1d)
     if (c.dparams) cudaFree(c.dparams);
@@ -890,6 +924,7 @@ wp_status batch_compile(wp_batch* b) {
   if (!b->idx2d.empty()) {
     std::vector<PassParams<T>> pz, px;
     std::vector<PrepParams<T>> pp;
+    std::vector<LinesParams<T>> pl;
     std::vector<int64_t> tz, tx;
     int64_t az = 0, ax = 0;
     for (int k : b->idx2d) {
@@ -915,6 +950,8 @@ wp_status batch_compile(wp_batch* b) {
       q.pot = h->dpot;
       q.ctrl = h->ctrl;
       pp.push_back(q);
+      pl.push_back(phase_lines_params<T>(h));
+      b->max_lines = std::max(b->max_lines, h->nlines_phase);
       b->smem2d = std::max(b->smem2d, std::max(h->plan[0].smem, h->plan[1].smem));
     }
     b->ntiles_z = az;
@@ -922,6 +959,8 @@ wp_status batch_compile(wp_batch* b) {
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_z, pz.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_x, px.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_prep, pp.size() * sizeof(PrepParams<T>)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_lines, pl.size() * sizeof(LinesParams<T>)));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_lines, pl.data(), pl.size() * sizeof(LinesParams<T>), cudaMemcpyHostToDevice));
     WP_CUDA(nullptr, cudaMalloc(&b->d_tiles_z, tz.size() * sizeof(int64_t)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_tiles_x, tx.size() * sizeof(int64_t)));
     WP_CUDA(nullptr, cudaMemcpy(b->d_pass_z, pz.data(), pz.size() * sizeof(PassParams<T>), cudaMemcpyHostToDevice));
@@ -929,6 +968,16 @@ wp_status batch_compile(wp_batch* b) {
     WP_CUDA(nullptr, cudaMemcpy(b->d_prep, pp.data(), pp.size() * sizeof(PrepParams<T>), cudaMemcpyHostToDevice));
     WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_z, tz.data(), tz.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_x, tx.data(), tx.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    std::vector<int> bz((size_t)az), bx((size_t)ax);
+    for (size_t k = 0; k < b->idx2d.size(); k++) {
+      const wp_handle* h = b->inst[b->idx2d[k]];
+      for (int64_t t = 0; t < h->plan[1].ntiles; t++) bz[(size_t)(tz[k] + t)] = (int)k;
+      for (int64_t t = 0; t < h->plan[0].ntiles; t++) bx[(size_t)(tx[k] + t)] = (int)k;
+    }
+    WP_CUDA(nullptr, cudaMalloc(&b->d_binst_z, bz.size() * sizeof(int)));
+    WP_CUDA(nullptr, cudaMalloc(&b->d_binst_x, bx.size() * sizeof(int)));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_binst_z, bz.data(), bz.size() * sizeof(int), cudaMemcpyHostToDevice));
+    WP_CUDA(nullptr, cudaMemcpy(b->d_binst_x, bx.data(), bx.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
   b->dirty = false;
   return WP_OK;
@@ -941,32 +990,45 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
   const int n2 = (int)b->idx2d.size();
   auto prep = [&](int add, double shift, double tau) -> wp_status {
     b->launches++;
-    return launch_rc(nullptr, launch_prep_batch<T>((const PrepParams<T>*)b->d_prep, n2, add, shift, tau, st),
-                     "batched prep");
+    wp_status r = launch_rc(nullptr, launch_prep_batch<T>((const PrepParams<T>*)b->d_prep, n2, add, shift, tau, st),
+                            "batched prep");
+    if (r != WP_OK || tau == 0.0) return r;
+    b->launches++;
+    return launch_rc(nullptr, launch_lines_batch<T>((const LinesParams<T>*)b->d_lines, n2, b->max_lines, st),
+                     "batched line records");
   };
   auto zpass = [&](uint32_t f) -> wp_status {
     b->launches++;
     return launch_rc(nullptr,
-                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, n2, b->ntiles_z, f, 0,
-                                          b->smem2d, st),
+                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, b->d_binst_z, b->ntiles_z,
+                                          f, 0, b->smem2d, st),
                      "batched pass");
   };
   auto xpass = [&](int khalf) -> wp_status {
     b->launches++;
     return launch_rc(nullptr,
-                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, n2, b->ntiles_x, F_KIN,
-                                          khalf, b->smem2d, st),
+                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, b->d_binst_x, b->ntiles_x,
+                                          F_KIN, khalf, b->smem2d, st),
                      "batched pass");
   };
   wp_status s2;
+  // the 1-D classes run on a side stream forked from, and joined back into, the batch
+  // stream, so they overlap the 2-D passes
+  const bool fork = !b->classes1d.empty() && n2 > 0 && b->side;
+  cudaStream_t st1 = fork ? b->side : st;
+  if (fork) {
+    WP_CUDA(nullptr, cudaEventRecord(b->fork_ev, st));
+    WP_CUDA(nullptr, cudaStreamWaitEvent(b->side, b->fork_ev, 0));
+  }
   for (auto& c : b->classes1d) {
     b->launches++;
     s2 = launch_rc(nullptr,
                    launch_res1d_batch<T>((const Res1dParams<T>*)c.dparams, (int)c.idx.size(), c.nthreads, c.ept, m,
-                                         c.smem, st),
+                                         c.smem, st1),
                    "batched 1-D kernel");
     if (s2 != WP_OK) return s2;
   }
+  if (fork) WP_CUDA(nullptr, cudaEventRecord(b->join_ev, b->side));
   if (n2 > 0) {
     if (b->order2d == WP_ORDER_VKV) {
       if ((s2 = prep(0, 0.0, 0.5)) != WP_OK || (s2 = zpass(F_PHASE | F_FFT)) != WP_OK || (s2 = xpass(0)) != WP_OK)
@@ -991,6 +1053,7 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
     if ((s2 = chunk_seq<T>(h, m, false)) != WP_OK) return s2;
     h->host_step = save;  // advanced uniformly below
   }
+  if (fork) WP_CUDA(nullptr, cudaStreamWaitEvent(st, b->join_ev, 0));
   return WP_OK;
 }
 
@@ -1327,6 +1390,12 @@ wp_status wp_batch_create(int32_t precision, void* stream, wp_batch** out) {
     }
     b->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+    wp_batch_destroy(b);
+    return fail(nullptr, WP_ECUDA, "stream or event creation");
+  }
   *out = b;
   return WP_OK;
 }
@@ -1377,9 +1446,13 @@ int64_t wp_batch_launch_count(const wp_batch* b) {
 wp_status wp_batch_destroy(wp_batch* b) {
   if (!b) return WP_OK;
   cudaStreamSynchronize(b->stream);
+  if (b->side) cudaStreamSynchronize(b->side);
   batch_free_compiled(b);
   for (wp_handle* h : b->inst) wp_destroy(h);
-  if (b->own_stream) cudaStreamDestroy(b->stream);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
   return WP_OK;
 }

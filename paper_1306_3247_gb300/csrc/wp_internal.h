@@ -178,6 +178,8 @@ struct PassParams {
   const TwE<T>* Krec;      // pass-axis kinetic records
   const cx<T>* Khalf_axes[3];     // dt/2 kinetic factors (batched kinetic pass, KVK ends)
   const cx<T>* Khalf_lo_axes[3];
+  const TwE<T>* Krec_half;        // dt/2 records of the pass axis
+  const LineRec<T>* lines_kin_half;
   const LineRec<T>* lines_phase;
   const LineRec<T>* lines_kin;
 };
@@ -270,8 +272,11 @@ template <class T> int launch_convert(const ConvParams<T>& p, void* stream);
 template <class T> int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream);
 template <class T> int launch_lines(const LinesParams<T>& p, void* stream);
 // batched launches (one block range per instance)
-template <class T> int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, int ninst,
-                                         int64_t ntiles, uint32_t flags, int khalf, size_t smem, void* stream);
+template <class T> int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start,
+                                         const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
+                                         size_t smem, void* stream);
+template <class T> int launch_lines_batch(const LinesParams<T>* params, int ninst, int64_t max_lines,
+                                          void* stream);
 template <class T> int launch_prep_batch(const PrepParams<T>* params, int ninst, int step_add, double shift_dt,
                                          double tau_dt, void* stream);
 template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept,

@@ -782,46 +782,71 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
 }
 
 // Batched pass over many instances: tile_start[k] is the first block of instance k (a
-// prefix sum of the instances' tile counts); every instance tiles its lines into
-// 2048-element tiles with 256 threads. The block finds its instance by binary search,
-// copies that instance's parameters to shared memory and runs the same pass body.
-template <class T>
-__global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
-                                                    const int64_t* __restrict__ tile_start, int ninst,
-                                                    uint32_t flags, int khalf) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
-  __shared__ int s_inst;
-  PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
-  if (threadIdx.x == 0) {
-    int lo = 0, hi = ninst - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (tile_start[mid] <= (int64_t)blockIdx.x)
-        lo = mid;
-      else
-        hi = mid - 1;
-    }
-    s_inst = lo;
+// prefix sum of the instances' tile counts) and block_inst[b] the instance of block b;
+// every instance tiles its lines into 2048-element tiles with 256 threads. The block
+// copies its instance's parameters to shared memory and runs the pass body: the
+// compile-time-shape body (with per-line records) for n = 64..1024, the run-time one
+// otherwise.
+template <class T, int LOGN, bool CONTIG>
+__device__ __forceinline__ void batch_fixed(const PassParams<T>& p, cx<T>* s, int64_t tile) {
+  const FixShape<LOGN, CONTIG> sh;
+  int64_t o0, cb;
+  tile_origin(p, sh, tile, o0, cb);
+  constexpr int C = 1 << FixShape<LOGN, CONTIG>::logC, NTOT = C << LOGN;
+  for (int e = threadIdx.x; e < NTOT; e += 256) {
+    const int i = e >> sh.logC, l = e & (C - 1);
+    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
   }
   __syncthreads();
-  const int inst = s_inst;
+  pass_compute<T, 8, false>(p, sh, s, tile);
+}
+
+template <class T, bool CONTIG>
+__global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
+                                                    const int64_t* __restrict__ tile_start,
+                                                    const int* __restrict__ block_inst, uint32_t flags, int khalf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
+  PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
+  const int inst = block_inst[blockIdx.x];
   const int* src = reinterpret_cast<const int*>(&params[inst]);
   for (int k = threadIdx.x; k < (int)(sizeof(PassParams<T>) / sizeof(int)); k += blockDim.x)
     reinterpret_cast<int*>(raw)[k] = src[k];
   __syncthreads();
   if (threadIdx.x == 0) {
     p.flags = flags;
-    if (khalf)
+    if (khalf) {
       for (int d = 0; d < 3; d++) {
         p.K[d] = p.Khalf_axes[d];
         p.K_lo[d] = p.Khalf_lo_axes[d];
       }
+      p.Krec = p.Krec_half;
+      p.lines_kin = p.lines_kin_half;
+    }
   }
   __syncthreads();
   const int64_t tile = (int64_t)blockIdx.x - tile_start[inst];
-  const DynShape sh(p);
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  switch (p.logn) {
+    case 6:
+      batch_fixed<T, 6, CONTIG>(p, s, tile);
+      return;
+    case 7:
+      batch_fixed<T, 7, CONTIG>(p, s, tile);
+      return;
+    case 8:
+      batch_fixed<T, 8, CONTIG>(p, s, tile);
+      return;
+    case 9:
+      batch_fixed<T, 9, CONTIG>(p, s, tile);
+      return;
+    case 10:
+      batch_fixed<T, 10, CONTIG>(p, s, tile);
+      return;
+    default:
+      break;
+  }
+  const DynShape sh(p);
   int64_t o0, cb;
   tile_origin(p, sh, tile, o0, cb);
   const int C = 1 << sh.logC, ntot = C << sh.logn;
@@ -831,6 +856,21 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
   }
   __syncthreads();
   pass_compute<T, 8, false>(p, sh, s, tile);
+}
+
+template <class T>
+__device__ void lines_body(const LinesParams<T>& p);
+
+// Batched per-line records: blockIdx.y selects the instance, x strides over its lines.
+template <class T>
+__global__ void __launch_bounds__(256) k_lines_batch(const LinesParams<T>* __restrict__ params) {
+  __shared__ __align__(16) unsigned char raw[sizeof(LinesParams<T>)];
+  const int* src = reinterpret_cast<const int*>(&params[blockIdx.y]);
+  for (int k = threadIdx.x; k < (int)(sizeof(LinesParams<T>) / sizeof(int)); k += blockDim.x)
+    reinterpret_cast<int*>(raw)[k] = src[k];
+  __syncthreads();
+  const LinesParams<T>& p = *reinterpret_cast<const LinesParams<T>*>(raw);
+  lines_body<T>(p);
 }
 
 // Fixed-size pass: n = 2^LOGN points per line, 2048-element tiles, 256 threads.
@@ -845,7 +885,7 @@ __global__ void __launch_bounds__(256) k_pass_fixed(const PassParams<T> p) {
 // low table parts), rounded to a record, and the per-line Gaussian-term phase
 // coefficients. Grid-stride over the lines.
 template <class T>
-__global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
+__device__ void lines_body(const LinesParams<T>& p) {
   const bool contig = (p.axis == p.g.ndim - 1);
   for (int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; line < p.nlines;
        line += (int64_t)gridDim.x * blockDim.x) {
@@ -876,6 +916,11 @@ __global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
     }
     p.out[line] = rec;
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
+  lines_body<T>(p);
 }
 
 // ------------------------------------------------------------------ per-step tables

@@ -101,15 +101,32 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
 }
 
 template <class T>
-int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, int ninst, int64_t ntiles,
+int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t ntiles,
                       uint32_t flags, int khalf, size_t smem, void* stream) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_pass_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_pass_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(k_pass_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     attr = true;
   }
-  if (ntiles > 0)
-    k_pass_batch<T><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, ninst, flags, khalf);
+  // the contiguous pass carries the potential phase, the strided one the kinetic factor
+  const bool contig = (flags & F_KIN) == 0;
+  if (ntiles > 0) {
+    if (contig)
+      k_pass_batch<T, true><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, block_inst,
+                                                                                  flags, khalf);
+    else
+      k_pass_batch<T, false><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, block_inst,
+                                                                                   flags, khalf);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
+int launch_lines_batch(const LinesParams<T>* params, int ninst, int64_t max_lines, void* stream) {
+  int64_t bx = (max_lines + 255) / 256;
+  if (bx > 64) bx = 64;
+  if (ninst > 0 && bx > 0) k_lines_batch<T><<<dim3((unsigned)bx, (unsigned)ninst), 256, 0, (cudaStream_t)stream>>>(params);
   return cuda_status(cudaGetLastError());
 }
 
@@ -153,9 +170,10 @@ int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, in
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
   template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
   template int launch_lines<T>(const LinesParams<T>&, void*);                    \
-  template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, int, int64_t, uint32_t, int, size_t,  \
+  template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, const int*, int64_t, uint32_t, int, size_t, \
                                     void*);                                      \
   template int launch_prep_batch<T>(const PrepParams<T>*, int, int, double, double, void*);                    \
+  template int launch_lines_batch<T>(const LinesParams<T>*, int, int64_t, void*);                              \
   template int launch_res1d_batch<T>(const Res1dParams<T>*, int, int, int, int64_t, size_t, void*);
 
 }  // namespace wp
