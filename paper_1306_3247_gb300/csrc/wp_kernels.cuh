@@ -621,6 +621,40 @@ __device__ __forceinline__ int64_t tile_gidx(const PassParams<T>& p, const SH& s
   return sh.contig ? ((o0 + l) << sh.logn) + i : (((o0 << sh.logn) + i) << p.log_inner) + cb + l;
 }
 
+// Fixed-shape tiles: 256 threads, 2048 elements. Thread t always serves line
+// l = t mod C and the points i = t / C + k 256 / C (k = 0..7), so its global addresses are a
+// base pointer plus a constant stride: no per-element 64-bit index arithmetic.
+template <class T, class SH>
+__device__ __forceinline__ void fixed_walk(const PassParams<T>& p, int64_t o0, int64_t cb, int& l, int& i0,
+                                           int64_t& base, int64_t& estride) {
+  l = threadIdx.x & ((1 << SH::logC) - 1);
+  i0 = threadIdx.x >> SH::logC;
+  if (SH::contig) {
+    base = ((o0 + l) << SH::logn) + i0;
+    estride = 1;
+  } else {
+    estride = int64_t(1) << p.log_inner;
+    base = (((o0 << SH::logn) + i0) << p.log_inner) + cb + l;
+  }
+}
+
+template <class T, class SH>
+__device__ __forceinline__ void fixed_load(const PassParams<T>& p, cx<T>* s, int64_t tile) {
+  constexpr int ISTEP = 256 >> SH::logC;
+  int64_t o0, cb;
+  tile_origin(p, SH(), tile, o0, cb);
+  int l, i0;
+  int64_t base, es;
+  fixed_walk<T, SH>(p, o0, cb, l, i0, base, es);
+  const cx<T>* src = p.in + base;
+  const int64_t step = es * ISTEP;
+  cx<T> v[8];
+#pragma unroll
+  for (int k = 0; k < 8; k++) v[k] = src[k * step];
+#pragma unroll
+  for (int k = 0; k < 8; k++) s[(i0 + k * ISTEP) * SH::LS + l] = v[k];
+}
+
 // Everything a pass does once its tile is in shared memory: the transforms and factors
 // selected by the flags, the store, the partial sums. Ends with a block barrier.
 template <class T, int E, bool OBS, class SH>
@@ -657,6 +691,25 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
     }
     const cx<T>* Pa = p.P[p.axis];
     const cx<T>* Pal = p.P_lo[p.axis];
+    if constexpr (SH::fixed) {
+      if (!(OBS && (f & F_OBS_POS))) {
+        // phase only: thread-fixed line record, points i0 + k 256/C
+        constexpr int ISTEP = 256 >> SH::logC;
+        const int l = tid & (C - 1), i0 = tid >> logC;
+        const LineRec<T> rec = sRec[l];
+        const T* G0 = p.G[0][p.axis];
+        const T* G1 = p.G[1][p.axis];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int i = i0 + k * ISTEP;
+          cx<T> v = apply_factor_rec(s[i * LS + l], p.Prec[i], rec.L);
+          if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
+          if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
+          s[i * LS + l] = v;
+        }
+        goto phase_done;
+      }
+    }
     for (int e = tid; e < ntot; e += nthr) {
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
@@ -699,6 +752,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
         }
       }
     }
+  phase_done:
     __syncthreads();
   }
 
@@ -715,6 +769,19 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
     }
     const cx<T>* Ka = p.K[p.axis];
     const cx<T>* Kal = p.K_lo[p.axis];
+    if constexpr (SH::fixed) {
+      if (!(OBS && (f & F_OBS_MOM))) {
+        constexpr int ISTEP = 256 >> SH::logC;
+        const int l = tid & (C - 1), i0 = tid >> logC;
+        const TwE<T> L = sRec[l].L;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int i = i0 + k * ISTEP;
+          s[i * LS + l] = apply_factor_rec(s[i * LS + l], p.Krec[i], L);
+        }
+        goto kin_done;
+      }
+    }
     for (int e = tid; e < ntot; e += nthr) {
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
@@ -740,14 +807,26 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
       }
     }
+  kin_done:
     __syncthreads();
     if (f & F_KIN) tile_fft<T, E, true>(s, p, sh, tid);
   }
 
   if (!(f & F_NO_STORE)) {
-    for (int e = tid; e < ntot; e += nthr) {
-      const int i = e >> logC, l = e & (C - 1);
-      p.out[tile_gidx(p, sh, o0, cb, i, l)] = s[i * LS + l];
+    if constexpr (SH::fixed) {
+      constexpr int ISTEP = 256 >> SH::logC;
+      int l, i0;
+      int64_t base, es;
+      fixed_walk<T, SH>(p, o0, cb, l, i0, base, es);
+      cx<T>* dst = p.out + base;
+      const int64_t step = es * ISTEP;
+#pragma unroll
+      for (int k = 0; k < 8; k++) dst[k * step] = s[(i0 + k * ISTEP) * LS + l];
+    } else {
+      for (int e = tid; e < ntot; e += nthr) {
+        const int i = e >> logC, l = e & (C - 1);
+        p.out[tile_gidx(p, sh, o0, cb, i, l)] = s[i * LS + l];
+      }
     }
   }
 
@@ -762,12 +841,16 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
 template <class T, int E, bool OBS, class SH>
 __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, cx<T>* s) {
   const int64_t tile = blockIdx.x;
-  int64_t o0, cb;
-  tile_origin(p, sh, tile, o0, cb);
-  const int C = 1 << sh.logC, ntot = C << sh.logn;
-  for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
-    const int i = e >> sh.logC, l = e & (C - 1);
-    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
+  if constexpr (SH::fixed) {
+    fixed_load<T, SH>(p, s, tile);
+  } else {
+    int64_t o0, cb;
+    tile_origin(p, sh, tile, o0, cb);
+    const int C = 1 << sh.logC, ntot = C << sh.logn;
+    for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
+      const int i = e >> sh.logC, l = e & (C - 1);
+      s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
+    }
   }
   __syncthreads();
   pass_compute<T, E, OBS>(p, sh, s, tile);
@@ -790,13 +873,7 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
 template <class T, int LOGN, bool CONTIG>
 __device__ __forceinline__ void batch_fixed(const PassParams<T>& p, cx<T>* s, int64_t tile) {
   const FixShape<LOGN, CONTIG> sh;
-  int64_t o0, cb;
-  tile_origin(p, sh, tile, o0, cb);
-  constexpr int C = 1 << FixShape<LOGN, CONTIG>::logC, NTOT = C << LOGN;
-  for (int e = threadIdx.x; e < NTOT; e += 256) {
-    const int i = e >> sh.logC, l = e & (C - 1);
-    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
-  }
+  fixed_load<T, FixShape<LOGN, CONTIG>>(p, s, tile);
   __syncthreads();
   pass_compute<T, 8, false>(p, sh, s, tile);
 }
