@@ -269,6 +269,7 @@ wp_status alloc_tables(wp_handle* h) {
   size_t off_lo[3][4];
   size_t off_st[3];
   size_t off_rec[3][3];
+  size_t off_obs[3][3];
   for (int d = 0; d < h->ndim; d++) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
@@ -278,6 +279,9 @@ wp_status alloc_tables(wp_handle* h) {
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][4 + gg] = add(n * sizeof(T));
     off[d][4 + WP_MAX_GAUSS] = add(n * sizeof(double));
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][5 + WP_MAX_GAUSS + gg] = add(n * sizeof(double));
+    off_obs[d][0] = add(n * sizeof(cx<T>));
+    off_obs[d][1] = add(n * sizeof(cx<T>));
+    off_obs[d][2] = add(n * sizeof(T));
   }
   WP_CUDA(h, cudaMalloc(&h->tabmem, bytes));
   WP_CUDA(h, cudaMemsetAsync(h->tabmem, 0, bytes, h->stream));
@@ -300,6 +304,9 @@ wp_status alloc_tables(wp_handle* h) {
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].G[gg] = (T*)(base + off[d][4 + gg]);
     tb[d].A = (double*)(base + off[d][4 + WP_MAX_GAUSS]);
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) tb[d].Gd[gg] = (double*)(base + off[d][5 + WP_MAX_GAUSS + gg]);
+    tb[d].Ox = (cx<T>*)(base + off_obs[d][0]);
+    tb[d].Ok = (cx<T>*)(base + off_obs[d][1]);
+    tb[d].AT = (T*)(base + off_obs[d][2]);
   }
   // static tables (high and low parts)
   for (int d = 0; d < h->ndim; d++) {
@@ -344,6 +351,19 @@ wp_status alloc_tables(wp_handle* h) {
         ls += lr;
       }
       WP_CUDA(h, cudaMemcpy(tb[d].Wst, rec.data(), rec.size(), cudaMemcpyHostToDevice));
+    }
+    {
+      // coordinates and wavenumbers (and their squares) of the axis, rounded to T
+      std::vector<cx<T>> ox(n), ok(n);
+      for (size_t i = 0; i < n; i++) {
+        const double x = h->g.xmin[d] + (double)i * h->g.dx[d];
+        const int64_t js = (int64_t)i < (int64_t)(n / 2) ? (int64_t)i : (int64_t)i - (int64_t)n;
+        const double k = h->g.kscale[d] * (double)js;
+        ox[i] = cx<T>{(T)x, (T)(x * x)};
+        ok[i] = cx<T>{(T)k, (T)(k * k)};
+      }
+      WP_CUDA(h, cudaMemcpy(tb[d].Ox, ox.data(), nb, cudaMemcpyHostToDevice));
+      WP_CUDA(h, cudaMemcpy(tb[d].Ok, ok.data(), nb, cudaMemcpyHostToDevice));
     }
     const double scale = d == 0 ? 1.0 / (double)h->N : 1.0;
     std::vector<TwE<T>> recs(n);
@@ -411,6 +431,9 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
     p.Khalf_axes[d] = tb[d].Khalf;
     p.Khalf_lo_axes[d] = tb[d].Khalf_lo;
   }
+  p.Ox = tb[axis].Ox;
+  p.Ok = tb[axis].Ok;
+  p.AT = tb[axis].AT;
   return p;
 }
 

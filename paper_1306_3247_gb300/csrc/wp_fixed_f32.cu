@@ -1,63 +1,4 @@
-// Fixed-size pass kernels (n = 64..1024 points per line, 2048-element tiles) for the
-// complex64 (FP32) form, in a translation unit of their own so that they compile in parallel.
-#include "wp_kernels.cuh"
+// Fixed-size pass kernels without partial sums for the complex64 form.
+#include "wp_fixed_launch.cuh"
 
-namespace wp {
-
-namespace {
-
-template <int LOGN>
-void launch_n(const PassParams<float>& p, unsigned ntiles, size_t smem, cudaStream_t st) {
-  if (p.log_inner == 0)
-    k_pass_fixed<float, LOGN, true, false><<<ntiles, 256, smem, st>>>(p);
-  else
-    k_pass_fixed<float, LOGN, false, false><<<ntiles, 256, smem, st>>>(p);
-}
-
-template <int LOGN>
-cudaError_t set_limit(int smem) {
-  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_fixed<float, LOGN, true, false>, a, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_fixed<float, LOGN, false, false>, a, smem);
-  return e;
-}
-
-}  // namespace
-
-template <>
-int launch_fixed<float>(const PassParams<float>& p, unsigned ntiles, size_t smem, void* stream) {
-  cudaStream_t st = (cudaStream_t)stream;
-  switch (p.logn) {
-    case 6:
-      launch_n<6>(p, ntiles, smem, st);
-      break;
-    case 7:
-      launch_n<7>(p, ntiles, smem, st);
-      break;
-    case 8:
-      launch_n<8>(p, ntiles, smem, st);
-      break;
-    case 9:
-      launch_n<9>(p, ntiles, smem, st);
-      break;
-    case 10:
-      launch_n<10>(p, ntiles, smem, st);
-      break;
-    default:
-      return (int)cudaErrorInvalidConfiguration;
-  }
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? 0 : (int)e;
-}
-
-template <>
-int fixed_smem_limit_set<float>(size_t smem) {
-  cudaError_t e = set_limit<6>((int)smem);
-  if (e == cudaSuccess) e = set_limit<7>((int)smem);
-  if (e == cudaSuccess) e = set_limit<8>((int)smem);
-  if (e == cudaSuccess) e = set_limit<9>((int)smem);
-  if (e == cudaSuccess) e = set_limit<10>((int)smem);
-  return e == cudaSuccess ? 0 : (int)e;
-}
-
-}  // namespace wp
+WP_FIXED_TU(float, false, launch_fixed, fixed_smem_limit_set)

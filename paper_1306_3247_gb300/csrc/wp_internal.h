@@ -143,6 +143,9 @@ struct AxisTab {
   T* G[WP_MAX_GAUSS];         // Gaussian-term factors exp(-((x - c)/w)^2)
   double* A;                  // additive potential A(x,t), FP64
   double* Gd[WP_MAX_GAUSS];   // Gaussian factors, FP64
+  cx<T>* Ox;                  // (x_i, x_i^2) in T: line sums of the position moments
+  cx<T>* Ok;                  // (k_i, k_i^2) in T: line sums of the momentum moments
+  T* AT;                      // A(x,t) rounded to T: line sums of the potential energy
 };
 
 template <class T>
@@ -182,6 +185,9 @@ struct PassParams {
   const LineRec<T>* lines_kin_half;
   const LineRec<T>* lines_phase;
   const LineRec<T>* lines_kin;
+  const cx<T>* Ox;     // pass-axis observable tables (fixed-size kernels)
+  const cx<T>* Ok;
+  const T* AT;
 };
 
 // Per-line records of one pass (k_lines).
@@ -288,6 +294,15 @@ template <class T> int pass_smem_limit_set(size_t smem);
 // fixed-size pass kernels (their own translation units, wp_fixed_*.cu)
 template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 template <class T> int fixed_smem_limit_set(size_t smem);
+// batched pass kernels, contiguous and strided axis (wp_batch_*.cu)
+template <class T> int launch_pass_batch_contig(const PassParams<T>* params, const int64_t* tile_start,
+                                                const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
+                                                size_t smem, void* stream);
+template <class T> int launch_pass_batch_strided(const PassParams<T>* params, const int64_t* tile_start,
+                                                 const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
+                                                 size_t smem, void* stream);
+template <class T> int launch_fixed_obs(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
+template <class T> int fixed_obs_smem_limit_set(size_t smem);
 template <class T> int res1d_smem_limit_set(size_t smem);
 
 // Kernel classes for timing and launch counting.

@@ -59,6 +59,31 @@ __device__ __forceinline__ cx<ff> cmulc(cx<ff> a, cx<ff> b) {
   return mk(ff_dot2(a.re, b.re, a.im, b.im, 1.f), ff_dot2(a.im, b.re, a.re, b.im, -1.f));
 }
 
+// Real helpers of the line sums in the element type: zero, |v|^2, a b + c, warp exchange,
+// conversion to FP64. Float-float uses error-free products and sums throughout.
+template <class T>
+__device__ __forceinline__ T tzero() {
+  return T(0);
+}
+template <>
+__device__ __forceinline__ ff tzero<ff>() {
+  return ff_make(0.f, 0.f);
+}
+__device__ __forceinline__ float norm2(cx<float> v) { return fmaf(v.re, v.re, v.im * v.im); }
+__device__ __forceinline__ double norm2(cx<double> v) { return fma(v.re, v.re, v.im * v.im); }
+__device__ __forceinline__ ff norm2(cx<ff> v) { return ff_dot2(v.re, v.re, v.im, v.im, 1.f); }
+__device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double madd(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ ff madd(ff a, ff b, ff c) { return c + a * b; }
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ ff shfl_xor(ff v, int o) {
+  return ff_make(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+}
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(ff v) { return (double)v; }
+
 // ------------------------------------------------------------------ butterflies
 // DFT of length R in registers, natural order in and out:
 // X_k = sum_r x_r exp(-+ 2 pi i r k / R) (minus forward, plus inverse).
@@ -655,6 +680,91 @@ __device__ __forceinline__ void fixed_load(const PassParams<T>& p, cx<T>* s, int
   for (int k = 0; k < 8; k++) s[(i0 + k * ISTEP) * SH::LS + l] = v[k];
 }
 
+// Block partials of the observable sums in a fixed-size kernel. Thread t holds the sums
+// of line l = t mod C over its 8 points (q[0..7], in T). The lanes of a line are combined
+// by xor shuffles, the 8 warps through the tile buffer, in a fixed order. Each line then
+// adds its part of the 16 sums in FP64: the pass-axis moments come from the line sums,
+// the other axes' coordinates, wavenumbers, potential parts and Gaussian factors are
+// constant along the line (Tab. 3 quantities; the potential is a sum of per-axis parts
+// and products of per-axis Gaussian factors). Partials of block b go to partials[b].
+template <class T, class SH>
+__device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[8], int64_t o0, int64_t cb,
+                                                 T* scratch, double (*red)[NQ]) {
+  constexpr int C = 1 << SH::logC;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int o = C; o < 32; o <<= 1)
+#pragma unroll
+    for (int j = 0; j < 8; j++) q[j] = q[j] + shfl_xor(q[j], o);
+  if (lane < C)
+#pragma unroll
+    for (int j = 0; j < 8; j++) scratch[(warp * C + lane) * 8 + j] = q[j];
+  __syncthreads();
+  if (tid < 8 * C) {
+    const int l = tid >> 3, j = tid & 7;
+    T sum = scratch[l * 8 + j];
+#pragma unroll
+    for (int w = 1; w < 8; w++) sum = sum + scratch[(w * C + l) * 8 + j];
+    red[l][j] = to_f64(sum);
+  }
+  __syncthreads();
+  double lt[8];
+  if (tid < C)
+#pragma unroll
+    for (int j = 0; j < 8; j++) lt[j] = red[tid][j];
+  __syncthreads();
+  if (tid < C) {
+    const int l = tid, ax = p.axis;
+    double* c = red[l];
+    for (int k = 0; k < NQ; k++) c[k] = 0.0;
+    int gi[3];
+    if (SH::contig)
+      grid_index(p.g, ax, o0 + l, 0, 0, gi);
+    else
+      grid_index(p.g, ax, o0, cb + l, 0, gi);
+    if (p.flags & F_OBS_POS) {
+      c[Q_RHO] = lt[0];
+      c[Q_X + ax] = lt[1];
+      c[Q_XX + ax] = lt[2];
+      double A = 0.0;
+      for (int d = 0; d < p.g.ndim; d++) {
+        if (d == ax) continue;
+        const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
+        c[Q_X + d] = x * lt[0];
+        c[Q_XX + d] = x * x * lt[0];
+        A += p.A[d][gi[d]];
+      }
+      double v = lt[3] + A * lt[0];
+      for (int gg = 0; gg < p.ngauss; gg++) {
+        double prod = p.ctrl->gcoef[gg];
+        for (int d = 0; d < p.g.ndim; d++)
+          if (d != ax) prod *= p.Gd[gg][d][gi[d]];
+        v += prod * lt[4 + gg];
+      }
+      c[Q_V] = v;
+      c[Q_AC_RE] = lt[6];
+      c[Q_AC_IM] = lt[7];
+    } else {
+      c[Q_RHOK] = lt[0];
+      c[Q_K + ax] = lt[1];
+      double k2 = 0.0;
+      for (int d = 0; d < p.g.ndim; d++) {
+        if (d == ax) continue;
+        const double k = wavenumber(p.g, d, gi[d]);
+        c[Q_K + d] = k * lt[0];
+        k2 += k * k;
+      }
+      c[Q_K2] = lt[2] + k2 * lt[0];
+    }
+  }
+  __syncthreads();
+  if (tid < NQ) {
+    double sum = 0.0;
+    for (int l = 0; l < C; l++) sum += red[l][tid];
+    p.partials[blockIdx.x * (int64_t)NQ + tid] = sum;
+  }
+}
+
 // Everything a pass does once its tile is in shared memory: the transforms and factors
 // selected by the flags, the store, the partial sums. Ends with a block barrier.
 template <class T, int E, bool OBS, class SH>
@@ -678,7 +788,10 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
 
   double acc[NQ];
 #pragma unroll
-  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  for (int k = 0; k < NQ; k++) acc[k] = 0.0;
+  T q[8];  // fixed-size kernels: the thread's line sums
+#pragma unroll
+  for (int k = 0; k < 8; k++) q[k] = tzero<T>();
 
   if (f & (F_PHASE | (OBS ? F_OBS_POS : 0u))) {
     if (f & F_PHASE) {
@@ -692,35 +805,61 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
     const cx<T>* Pa = p.P[p.axis];
     const cx<T>* Pal = p.P_lo[p.axis];
     if constexpr (SH::fixed) {
-      if (!(OBS && (f & F_OBS_POS))) {
-        // phase only: thread-fixed line record, points i0 + k 256/C
-        constexpr int ISTEP = 256 >> SH::logC;
-        const int l = tid & (C - 1), i0 = tid >> logC;
-        const LineRec<T> rec = sRec[l];
-        const T* G0 = p.G[0][p.axis];
-        const T* G1 = p.G[1][p.axis];
+      // thread-fixed line record, points i0 + k 256/C; with OBS also the thread's line
+      // sums of |psi|^2 times 1, x, x^2, A(x), the Gaussian factors, and conj(psi0) psi
+      constexpr int ISTEP = 256 >> SH::logC;
+      const int l = tid & (C - 1), i0 = tid >> logC;
+      const bool ph = !OBS || (f & F_PHASE);
+      LineRec<T> rec;
+      if (ph) rec = sRec[l];
+      const T* G0 = p.G[0][p.axis];
+      const T* G1 = p.G[1][p.axis];
+      [[maybe_unused]] const cx<T>* z0 = nullptr;
+      [[maybe_unused]] int64_t zstep = 0;
+      if constexpr (OBS) {
+        if (f & F_AUTOCORR) {
+          int ll, ii;
+          int64_t base, es;
+          fixed_walk<T, SH>(p, o0, cb, ll, ii, base, es);
+          z0 = p.psi0 + base;
+          zstep = es * ISTEP;
+        }
+      }
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const int i = i0 + k * ISTEP;
-          cx<T> v = apply_factor_rec(s[i * LS + l], p.Prec[i], rec.L);
+      for (int k = 0; k < 8; k++) {
+        const int i = i0 + k * ISTEP;
+        cx<T> v = s[i * LS + l];
+        if (ph) {
+          v = apply_factor_rec(v, p.Prec[i], rec.L);
           if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
           if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
           s[i * LS + l] = v;
         }
-        goto phase_done;
+        if constexpr (OBS) {
+          if (f & F_OBS_POS) {
+            const T rho = norm2(v);
+            const cx<T> xx = p.Ox[i];
+            q[0] = q[0] + rho;
+            q[1] = madd(xx.re, rho, q[1]);
+            q[2] = madd(xx.im, rho, q[2]);
+            q[3] = madd(p.AT[i], rho, q[3]);
+            if (p.ngauss > 0) q[4] = madd(G0[i], rho, q[4]);
+            if (p.ngauss > 1) q[5] = madd(G1[i], rho, q[5]);
+            if (f & F_AUTOCORR) {
+              const cx<T> c = cmulc(v, z0[k * zstep]);
+              q[6] = q[6] + c.re;
+              q[7] = q[7] + c.im;
+            }
+          }
+        }
       }
-    }
+    } else {
     for (int e = tid; e < ntot; e += nthr) {
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
       if (f & F_PHASE) {
-        if constexpr (SH::fixed) {
-          v = apply_factor_rec(v, p.Prec[i], sRec[l].L);
-          for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sRec[l].g[gg] * p.G[gg][p.axis][i]);
-        } else {
-          v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
-          for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
-        }
+        v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
+        for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
         s[i * LS + l] = v;
       }
       if (OBS && (f & F_OBS_POS)) {
@@ -752,7 +891,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
         }
       }
     }
-  phase_done:
+    }
     __syncthreads();
   }
 
@@ -770,18 +909,27 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
     const cx<T>* Ka = p.K[p.axis];
     const cx<T>* Kal = p.K_lo[p.axis];
     if constexpr (SH::fixed) {
-      if (!(OBS && (f & F_OBS_MOM))) {
-        constexpr int ISTEP = 256 >> SH::logC;
-        const int l = tid & (C - 1), i0 = tid >> logC;
-        const TwE<T> L = sRec[l].L;
+      // with OBS: the thread's line sums of |psi_hat|^2 times 1, k, k^2
+      constexpr int ISTEP = 256 >> SH::logC;
+      const int l = tid & (C - 1), i0 = tid >> logC;
+      const bool kin = !OBS || (f & F_KIN);
+      TwE<T> L;
+      if (kin) L = sRec[l].L;
 #pragma unroll
-        for (int k = 0; k < 8; k++) {
-          const int i = i0 + k * ISTEP;
-          s[i * LS + l] = apply_factor_rec(s[i * LS + l], p.Krec[i], L);
+      for (int k = 0; k < 8; k++) {
+        const int i = i0 + k * ISTEP;
+        if constexpr (OBS) {
+          if (f & F_OBS_MOM) {
+            const T rho = norm2(s[i * LS + l]);
+            const cx<T> kk = p.Ok[i];
+            q[0] = q[0] + rho;
+            q[1] = madd(kk.re, rho, q[1]);
+            q[2] = madd(kk.im, rho, q[2]);
+          }
         }
-        goto kin_done;
+        if (kin) s[i * LS + l] = apply_factor_rec(s[i * LS + l], p.Krec[i], L);
       }
-    }
+    } else {
     for (int e = tid; e < ntot; e += nthr) {
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
@@ -800,14 +948,9 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           acc[Q_K2] += k * k * rho;
         }
       }
-      if (f & F_KIN) {
-        if constexpr (SH::fixed)
-          s[i * LS + l] = apply_factor_rec(v, p.Krec[i], sRec[l].L);
-        else
-          s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
-      }
+      if (f & F_KIN) s[i * LS + l] = apply_factor(v, Ka[i], Kal[i], sLh[l], sLl[l]);
     }
-  kin_done:
+    }
     __syncthreads();
     if (f & F_KIN) tile_fft<T, E, true>(s, p, sh, tid);
   }
@@ -831,8 +974,13 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
   }
 
   if (OBS && (f & (F_OBS_POS | F_OBS_MOM))) {
-    block_sum(acc, tot, red);
-    if (tid < NQ) p.partials[blockIdx.x * (int64_t)NQ + tid] = tot[tid];
+    if constexpr (SH::fixed) {
+      __syncthreads();  // the tile is free now: it holds the per-warp line sums
+      fixed_obs_reduce<T, SH>(p, q, o0, cb, reinterpret_cast<T*>(s), red);
+    } else {
+      block_sum(acc, tot, red);
+      if (tid < NQ) p.partials[blockIdx.x * (int64_t)NQ + tid] = tot[tid];
+    }
   }
   __syncthreads();
 }
@@ -1025,6 +1173,7 @@ __device__ void prep_body(const PrepParams<T>& p) {
         if (part != 0.0) A += term_coef(tm, t) * part;
       }
       tb.A[i] = A;
+      if (tb.AT) tb.AT[i] = (T)A;
       double sn, cs;
       sincos(-A * p.tau / p.g.hbar, &sn, &cs);
       const T hc = (T)cs, hs = (T)sn;

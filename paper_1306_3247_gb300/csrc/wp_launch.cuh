@@ -11,6 +11,7 @@ static inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? 0 : (in
 template <class T>
 int pass_smem_limit_set(size_t smem) {
   cudaError_t e = (cudaError_t)fixed_smem_limit_set<T>(smem);
+  if (e == cudaSuccess) e = (cudaError_t)fixed_obs_smem_limit_set<T>(smem);
   const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, false>, (cudaFuncAttribute)a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, true>, (cudaFuncAttribute)a, (int)smem);
@@ -29,17 +30,22 @@ int res1d_smem_limit_set(size_t smem) {
   return cuda_status(e);
 }
 
-// p.fixed selects the fixed-size kernel (n = 64..1024, 2048-element tiles, 256 threads)
-// for passes without partial sums; otherwise p.ept selects the run-time variant (8 elements per thread: <= 256 threads;
+// p.fixed selects the fixed-size kernel (n = 64..1024, 2048-element tiles, 256 threads),
+// with partial sums when they are positions on the contiguous axis or momenta on a
+// strided one; otherwise p.ept selects the run-time variant (8 elements per thread: <= 256 threads;
 // 16: <= 512).
 template <class T>
 int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* stream) {
   const bool obs = (p.flags & (F_OBS_POS | F_OBS_MOM)) != 0;
   const dim3 grid((unsigned)ntiles), block(p.nthreads);
   cudaStream_t st = (cudaStream_t)stream;
-  if (p.fixed && !obs) {
+  if (p.fixed) {
     if (p.nthreads != 256 || p.logC != 11 - p.logn) return (int)cudaErrorInvalidConfiguration;
-    return launch_fixed<T>(p, grid.x, smem, stream);
+    if (!obs) return launch_fixed<T>(p, grid.x, smem, stream);
+    // the fixed variant sums positions on the contiguous axis, momenta on a strided one
+    const bool contig = p.log_inner == 0;
+    if ((contig && !(p.flags & F_OBS_MOM)) || (!contig && !(p.flags & F_OBS_POS)))
+      return launch_fixed_obs<T>(p, grid.x, smem, stream);
   }
   if (p.ept == 8 && p.nthreads <= 256) {
     if (obs)
@@ -103,23 +109,10 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
 template <class T>
 int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t ntiles,
                       uint32_t flags, int khalf, size_t smem, void* stream) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_pass_batch<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(k_pass_batch<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    attr = true;
-  }
   // the contiguous pass carries the potential phase, the strided one the kinetic factor
-  const bool contig = (flags & F_KIN) == 0;
-  if (ntiles > 0) {
-    if (contig)
-      k_pass_batch<T, true><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, block_inst,
-                                                                                  flags, khalf);
-    else
-      k_pass_batch<T, false><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, block_inst,
-                                                                                   flags, khalf);
-  }
-  return cuda_status(cudaGetLastError());
+  if ((flags & F_KIN) == 0)
+    return launch_pass_batch_contig<T>(params, tile_start, block_inst, ntiles, flags, khalf, smem, stream);
+  return launch_pass_batch_strided<T>(params, tile_start, block_inst, ntiles, flags, khalf, smem, stream);
 }
 
 template <class T>

@@ -146,13 +146,14 @@ def test_2d_laser_trap_c64():
     cfg, pb = small_laser_trap()
     terms = cfg["terms"]
     psi0 = O.gaussian(pb, **cfg["init"])
-    ref = O.propagate(pb, terms, psi0, 1000)
-    with WPK.Propagator(pb, terms, "c64") as P:
+    ref, ref_obs = O.run(pb, terms, psi0, 1000, 100)
+    with WPK.Propagator(pb, terms, "c64", autocorr=True) as P:
         P.set_state(psi0)
         obs = P.run(1000, 100)
         psi = P.get_state()
     assert rel_l2(psi, ref) < TOL64
     assert np.max(np.abs(obs["norm"] - obs["norm"][0])) < 1e-5
+    compare_obs(obs, ref_obs, TOL64)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c128f"])
@@ -198,13 +199,14 @@ def test_3d_barrier_c64():
     cfg, pb = small_barrier()
     terms = cfg["terms"]
     psi0 = O.gaussian(pb, **cfg["init"])
-    ref = O.propagate(pb, terms, psi0, 200)
-    with WPK.Propagator(pb, terms, "c64") as P:
+    ref, ref_obs = O.run(pb, terms, psi0, 200, 50)
+    with WPK.Propagator(pb, terms, "c64", autocorr=True) as P:
         P.set_state(psi0)
         obs = P.run(200, 50)
         psi = P.get_state()
     assert rel_l2(psi, ref) < TOL64
     assert np.max(np.abs(obs["norm"] - obs["norm"][0])) < 1e-5
+    compare_obs(obs, ref_obs, TOL64)
 
 
 @pytest.mark.parametrize("prec", ["c128", "c128f"])
