@@ -78,6 +78,8 @@ struct wp_handle {
   int res_nthreads = 32;
   int res_ept = 8;
   size_t res_smem = 0;
+  cx<double>* res_S = nullptr;     // 1-D static phase tables, 2 x n (dt, dt/2)
+  uint32_t res_plane_mask = 0, res_gen_mask = 0;
   int64_t host_step = 0;
   int64_t launches = 0;
   bool profiling = false;
@@ -529,7 +531,7 @@ wp_status ensure_obs(wp_handle* h, int64_t cap) {
 }
 
 template <class T>
-wp_status run_res1d(wp_handle* h, int64_t nsteps, bool obs) {
+Res1dParams<T> res1d_params(wp_handle* h) {
   Res1dParams<T> p{};
   AxisTab<T>* tb = tabs<T>(h);
   p.psi = (cx<T>*)h->state;
@@ -539,9 +541,7 @@ wp_status run_res1d(wp_handle* h, int64_t nsteps, bool obs) {
   p.nthreads = h->res_nthreads;
   p.ept = h->res_ept;
   p.order = h->pb.order;
-  p.obs = obs ? 1 : 0;
   p.autocorr = h->pb.autocorr ? 1 : 0;
-  p.nsteps = nsteps;
   p.W = tb[0].W;
   p.W_lo = tb[0].W_lo;
   p.Kfull = tb[0].Kfull;
@@ -552,6 +552,48 @@ wp_status run_res1d(wp_handle* h, int64_t nsteps, bool obs) {
   p.ctrl = h->ctrl;
   p.obs_out = h->obs_dev;
   p.obs_cap = h->obs_cap;
+  p.S[0] = h->res_S;
+  p.S[1] = h->res_S + h->n[0];
+  p.plane_mask = h->res_plane_mask;
+  p.gen_mask = h->res_gen_mask;
+  return p;
+}
+
+// Classifies the terms of a 1-D potential by time dependence and rebuilds the static
+// phase tables: linear and constant terms form a plane wave; terms with a constant
+// coefficient (A = 0) and a fixed centre (v = 0) are static; the rest are general.
+wp_status res1d_split_potential(wp_handle* h) {
+  uint32_t stat = 0, plane = 0, gen = 0;
+  for (int k = 0; k < h->hpot.nterms; k++) {
+    const wp_pot_term& t = h->hpot.term[k];
+    if (t.shape == WP_SHAPE_LINEAR || t.shape == WP_SHAPE_CONST)
+      plane |= 1u << k;
+    else if (t.A == 0.0 && t.v[0] == 0.0)
+      stat |= 1u << k;
+    else
+      gen |= 1u << k;
+  }
+  StaticPhaseParams sp{};
+  sp.g = h->g;
+  sp.n = h->n[0];
+  sp.pot = h->dpot;
+  sp.static_mask = stat;
+  sp.S[0] = h->res_S;
+  sp.S[1] = h->res_S + h->n[0];
+  const int rc = launch_static_phase(sp, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "static phase kernel");
+  // batched instances run on other streams: the tables are complete on return
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->res_plane_mask = plane;
+  h->res_gen_mask = gen;
+  return WP_OK;
+}
+
+template <class T>
+wp_status run_res1d(wp_handle* h, int64_t nsteps, bool obs) {
+  Res1dParams<T> p = res1d_params<T>(h);
+  p.obs = obs ? 1 : 0;
+  p.nsteps = nsteps;
   LaunchScope ls(h, K_RES1D);
   return launch_rc(h, launch_res1d<T>(p, h->res_smem, h->stream), "1-D resident kernel");
 }
@@ -917,28 +959,7 @@ wp_status batch_compile(wp_batch* b) {
     BatchClass1D c = kv.second;
     std::vector<Res1dParams<T>> ps;
     for (int k : c.idx) {
-      wp_handle* h = b->inst[k];
-      AxisTab<T>* tb = tabs<T>(h);
-      Res1dParams<T> p{};
-      p.psi = (cx<T>*)h->state;
-      p.psi0 = (const cx<T>*)h->psi0;
-      p.g = h->g;
-      p.logn = h->g.ln[0];
-      p.nthreads = h->res_nthreads;
-      p.ept = h->res_ept;
-      p.order = h->pb.order;
-      p.autocorr = h->pb.autocorr ? 1 : 0;
-      p.W = tb[0].W;
-      p.W_lo = tb[0].W_lo;
-      p.Kfull = tb[0].Kfull;
-      p.Khalf = tb[0].Khalf;
-      p.Kfull_lo = tb[0].Kfull_lo;
-      p.Khalf_lo = tb[0].Khalf_lo;
-      p.pot = h->dpot;
-      p.ctrl = h->ctrl;
-      p.obs_out = h->obs_dev;
-      p.obs_cap = h->obs_cap;
-      ps.push_back(p);
+      ps.push_back(res1d_params<T>(b->inst[k]));
     }
     WP_CUDA(nullptr, cudaMalloc(&c.dparams, ps.size() * sizeof(Res1dParams<T>)));
     WP_CUDA(nullptr, cudaMemcpy(c.dparams, ps.data(), ps.size() * sizeof(Res1dParams<T>), cudaMemcpyHostToDevice));
@@ -1233,7 +1254,9 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     h->plan[0] = make_plan(h, 0);
-
+    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)n * sizeof(cx<double>))) != cudaSuccess)
+      return bail(cuda_fail(h, e, "static phase allocation"));
+    if ((st = res1d_split_potential(h)) != WP_OK) return bail(st);
   }
   if ((st = ensure_obs(h, 64)) != WP_OK) return bail(st);
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "synchronize"));
@@ -1246,7 +1269,7 @@ wp_status wp_destroy(wp_handle* h) {
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
                   h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
-                  h->lines_kin[1]};
+                  h->lines_kin[1], h->res_S};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ep : h->pending) {
@@ -1282,6 +1305,7 @@ wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
   WP_CUDA(h, cudaMemcpy(h->dpot, &dp, sizeof(dp), cudaMemcpyHostToDevice));
   h->hpot = dp;
+  if (h->ndim == 1) return res1d_split_potential(h);
   return WP_OK;
 }
 

@@ -1228,27 +1228,69 @@ __global__ void __launch_bounds__(256) k_prep_batch(const PrepParams<T>* __restr
 // ------------------------------------------------------------------ 1-D resident kernel
 // One CTA holds one 1-D line in shared memory for a chunk of steps: the whole step
 // (potential phase, FFT, kinetic factor, inverse FFT) runs without touching HBM.
+// V(x,t) = sum_k f_k(t) s_k(x,t) split by time dependence (Eq. 9 applied with the terms of
+// Tab. 2): static terms come from the FP64 tables S (built once per potential), linear and
+// constant terms sum to beta(t) x - gamma(t), whose phase at x_j = xmin + j dx is the
+// plane wave exp(-i (theta0 + j delta)) = hiT[j / 64] loT[j mod 64] (both tables formed
+// per step with FP64 sincos of directly computed arguments), and the remaining terms are
+// evaluated at every point. The FP64 product of the factors is applied to the state.
 template <class T, int E>
-__device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, double t, double tau,
-                                      double* fco, int tid, int nthr) {
+__device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, double t, int half, double* fco,
+                                      cx<double>* hiT, cx<double>* loT, int tid, int nthr) {
   const DevPot& pot = *p.pot;
+  const double tau = half ? 0.5 * p.g.dt : p.g.dt;
+  const int n = 1 << p.logn;
   __syncthreads();
   if (tid < pot.nterms) fco[tid] = term_coef(pot.term[tid], t);
   __syncthreads();
-  const int n = 1 << p.logn;
-  for (int i = tid; i < n; i += nthr) {
-    const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
-    double V = 0.0;
+  const bool plane = p.plane_mask != 0;
+  if (plane) {
+    double beta = 0.0, gamma = 0.0;
     for (int k = 0; k < pot.nterms; k++) {
+      if (!((p.plane_mask >> k) & 1u)) continue;
       const wp_pot_term& tm = pot.term[k];
-      const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, t) : term_axis_part(tm, 0, x, t);
-      V += fco[k] * sh;
+      if (tm.shape == WP_SHAPE_LINEAR) {
+        beta += fco[k] * tm.a[0];
+        gamma += fco[k] * tm.a[0] * (tm.c0[0] + tm.v[0] * t);
+      } else {
+        gamma -= fco[k];
+      }
     }
-    double sn, cs;
-    sincos(-V * tau / p.g.hbar, &sn, &cs);
-    const T hc = (T)cs, hs = (T)sn;
+    const double th0 = tau * (beta * p.g.xmin[0] - gamma) / p.g.hbar;
+    const double del = tau * beta * p.g.dx[0] / p.g.hbar;
+    const int nhi = n > 64 ? n >> 6 : 1, nlo = n < 64 ? n : 64;
+    for (int k = tid; k < nhi + nlo; k += nthr) {
+      double sn, cs;
+      if (k < nhi) {
+        sincos(-fma((double)(k << 6), del, th0), &sn, &cs);
+        hiT[k] = mk(cs, sn);
+      } else {
+        sincos(-(double)(k - nhi) * del, &sn, &cs);
+        loT[k - nhi] = mk(cs, sn);
+      }
+    }
+    __syncthreads();
+  }
+  const cx<double>* S = p.S[half ? 1 : 0];
+  for (int i = tid; i < n; i += nthr) {
+    cx<double> fac = S[i];
+    if (plane) fac = cmul(fac, cmul(hiT[i >> 6], loT[i & 63]));
+    if (p.gen_mask) {
+      const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
+      double V = 0.0;
+      for (int k = 0; k < pot.nterms; k++) {
+        if (!((p.gen_mask >> k) & 1u)) continue;
+        const wp_pot_term& tm = pot.term[k];
+        const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, t) : term_axis_part(tm, 0, x, t);
+        V += fco[k] * sh;
+      }
+      double sn, cs;
+      sincos(-V * tau / p.g.hbar, &sn, &cs);
+      fac = cmul(fac, mk(cs, sn));
+    }
+    const T hc = (T)fac.re, hs = (T)fac.im;
     const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
-    s[i] = apply_factor(s[i], mk(hc, hs), mk((T)(cs - (double)hc), (T)(sn - (double)hs)), one, zero);
+    s[i] = apply_factor(s[i], mk(hc, hs), mk((T)(fac.re - (double)hc), (T)(fac.im - (double)hs)), one, zero);
   }
   __syncthreads();
 }
@@ -1269,6 +1311,7 @@ __device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
   __shared__ double red[32][NQ];
   __shared__ double qp[NQ], qm[NQ];
   __shared__ double fco[WP_MAX_TERMS];
+  __shared__ cx<double> hiT[256], loT[64];  // plane-wave tables (n <= 16384)
   const int tid = threadIdx.x, nthr = p.nthreads;
   const int n = 1 << p.logn;
   const int64_t s0 = p.ctrl->step;
@@ -1281,16 +1324,16 @@ __device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
   const int64_t m = p.nsteps;
   if (m > 0) {
     if (p.order == WP_ORDER_VKV) {
-      res1d_potential_phase<T, E>(s, p, tim(s0), 0.5 * dt, fco, tid, nthr);
+      res1d_potential_phase<T, E>(s, p, tim(s0), 1, fco, hiT, loT, tid, nthr);
       for (int64_t k = 0; k < m; k++) {
         res1d_kinetic<T, E>(s, p, p.Kfull, p.Kfull_lo, tid, nthr);
         const bool last = (k == m - 1);
-        res1d_potential_phase<T, E>(s, p, tim(s0 + k + 1), last ? 0.5 * dt : dt, fco, tid, nthr);
+        res1d_potential_phase<T, E>(s, p, tim(s0 + k + 1), last ? 1 : 0, fco, hiT, loT, tid, nthr);
       }
     } else {
       res1d_kinetic<T, E>(s, p, p.Khalf, p.Khalf_lo, tid, nthr);
       for (int64_t k = 0; k < m; k++) {
-        res1d_potential_phase<T, E>(s, p, tim(s0 + k) + 0.5 * dt, dt, fco, tid, nthr);
+        res1d_potential_phase<T, E>(s, p, tim(s0 + k) + 0.5 * dt, 0, fco, hiT, loT, tid, nthr);
         res1d_kinetic<T, E>(s, p, (k == m - 1) ? p.Khalf : p.Kfull, (k == m - 1) ? p.Khalf_lo : p.Kfull_lo, tid, nthr);
       }
     }
@@ -1377,6 +1420,28 @@ __global__ void __launch_bounds__(MAXT) k_res1d_batch(const Res1dParams<T>* __re
 }
 
 #ifdef WP_COMMON_KERNELS
+// ------------------------------------------------------------------ static phase tables
+// exp(-i V_s(x_j) tau / hbar) for tau = dt and dt/2, V_s the sum of the static terms
+// (time-independent coefficient and centre) of a 1-D potential, in FP64.
+__global__ void __launch_bounds__(256) k_static_phase(const StaticPhaseParams p) {
+  const DevPot& pot = *p.pot;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
+    double V = 0.0;
+    for (int k = 0; k < pot.nterms; k++) {
+      if (!((p.static_mask >> k) & 1u)) continue;
+      const wp_pot_term& tm = pot.term[k];
+      const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, 0.0) : term_axis_part(tm, 0, x, 0.0);
+      V += term_coef(tm, 0.0) * sh;
+    }
+    double sn, cs;
+    sincos(-V * p.g.dt / p.g.hbar, &sn, &cs);
+    p.S[0][i] = mk(cs, sn);
+    sincos(-V * (0.5 * p.g.dt) / p.g.hbar, &sn, &cs);
+    p.S[1][i] = mk(cs, sn);
+  }
+}
+
 // ------------------------------------------------------------------ reduction kernel
 // One block: sums the per-CTA partials in a fixed order and writes the observable record.
 __global__ void __launch_bounds__(256) k_reduce(const ReduceParams p) {
