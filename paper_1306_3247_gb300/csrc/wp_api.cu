@@ -78,6 +78,7 @@ struct wp_handle {
   int res_nthreads = 32;
   int res_ept = 8;
   size_t res_smem = 0;
+  bool res_fixed = false;          // 1-D line of compile-time length (k_res1d_fixed)
   cx<double>* res_S = nullptr;     // 1-D static phase tables, 2 x n (dt, dt/2)
   uint32_t res_plane_mask = 0, res_gen_mask = 0;
   int64_t host_step = 0;
@@ -556,6 +557,10 @@ Res1dParams<T> res1d_params(wp_handle* h) {
   p.S[1] = h->res_S + h->n[0];
   p.plane_mask = h->res_plane_mask;
   p.gen_mask = h->res_gen_mask;
+  p.fixed = h->res_fixed ? 1 : 0;
+  p.Wst = tb[0].Wst;
+  p.Krec[0] = tb[0].Kfull_rec;
+  p.Krec[1] = tb[0].Khalf_rec;
   return p;
 }
 
@@ -867,6 +872,7 @@ wp_status validate_problem(const wp_problem* pb) {
 // chunk length as a CUDA graph and replayed.
 struct BatchClass1D {
   int logn = 0, nthreads = 32, ept = 8;
+  bool fixed = false;
   size_t smem = 0;
   std::vector<int> idx;
   void* dparams = nullptr;
@@ -946,6 +952,7 @@ wp_status batch_compile(wp_batch* b) {
       c.logn = h->g.ln[0];
       c.nthreads = h->res_nthreads;
       c.ept = h->res_ept;
+      c.fixed = h->res_fixed;
       c.smem = h->res_smem;
       c.idx.push_back(k);
     } else if (batchable_2d(h) && (b->idx2d.empty() || h->pb.order == b->order2d)) {
@@ -1066,9 +1073,11 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
   }
   for (auto& c : b->classes1d) {
     b->launches++;
+    const auto* prm = (const Res1dParams<T>*)c.dparams;
+    const int ni = (int)c.idx.size();
     s2 = launch_rc(nullptr,
-                   launch_res1d_batch<T>((const Res1dParams<T>*)c.dparams, (int)c.idx.size(), c.nthreads, c.ept, m,
-                                         c.smem, st1),
+                   c.fixed ? launch_res1d_fixed_batch<T>(prm, ni, c.logn, m, c.smem, st1)
+                           : launch_res1d_batch<T>(prm, ni, c.nthreads, c.ept, m, c.smem, st1),
                    "batched 1-D kernel");
     if (s2 != WP_OK) return s2;
   }
@@ -1244,7 +1253,9 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
       return bail(cuda_fail(h, e, "partials allocation"));
   } else {
     const int64_t n = h->n[0];
-    const int E = n <= 2048 ? 8 : 16;
+    const int ln = h->g.ln[0];
+    h->res_fixed = ln >= kRes1dLogMin && ln <= (h->elem == 8 ? kRes1dLogMax : 13);
+    const int E = h->res_fixed ? wp_res1d_fixed_ept(ln) : (n <= 2048 ? 8 : 16);
     const int64_t thr = std::max<int64_t>(1, n / E);
     h->res_ept = E;
     h->res_nthreads = (int)((thr + 31) / 32 * 32);

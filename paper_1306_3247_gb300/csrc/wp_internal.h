@@ -58,6 +58,9 @@ __host__ __device__ constexpr int wp_stage_tw_offset(int logn, int logNs) {
   return off;
 }
 constexpr int kFixedLogMin = 6, kFixedLogMax = 10;  // fixed-size pass kernels: n = 64..1024
+constexpr int kRes1dLogMin = 8, kRes1dLogMax = 14;  // fixed-length resident lines: n = 256..16384
+// elements per thread of a fixed-length resident line (1024 threads at most)
+__host__ __device__ constexpr int wp_res1d_fixed_ept(int logn) { return logn >= 14 ? 16 : 8; }
 
 // A table factor as one 16-byte record: the value for FP64 and float-float, the high
 // and low FP32 parts for the complex64 form.
@@ -246,6 +249,9 @@ struct Res1dParams {
   const cx<double>* S[2];
   uint32_t plane_mask;
   uint32_t gen_mask;
+  int32_t fixed;             // compile-time line length (k_res1d_fixed), n = 2^8 .. 2^14
+  const void* Wst;           // per-stage twiddle records (fixed)
+  const TwE<T>* Krec[2];     // kinetic factors dt, dt/2 as records (fixed)
 };
 
 // FP64 static phase tables of a 1-D handle (k_static_phase).
@@ -321,6 +327,11 @@ template <class T> int launch_pass_batch_strided(const PassParams<T>* params, co
 template <class T> int launch_fixed_obs(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 template <class T> int fixed_obs_smem_limit_set(size_t smem);
 template <class T> int res1d_smem_limit_set(size_t smem);
+// fixed-length resident-line kernels (their own translation units, wp_res1d_*.cu)
+template <class T> int launch_res1d_fixed(const Res1dParams<T>& p, size_t smem, void* stream);
+template <class T> int launch_res1d_fixed_batch(const Res1dParams<T>* params, int ninst, int logn, int64_t nsteps,
+                                                size_t smem, void* stream);
+template <class T> int res1d_fixed_smem_limit_set(size_t smem);
 
 // Kernel classes for timing and launch counting.
 enum KernelClass : int {

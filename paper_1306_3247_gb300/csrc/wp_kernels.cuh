@@ -301,14 +301,14 @@ __device__ __forceinline__ cx<float> tw_apply(cx<float> v, const TwE<float>& e) 
   return INV ? cmulc2(v, e.h, e.l) : cmul2(v, e.h, e.l);
 }
 
-template <class T, int LOGN, int LOGC, int LS, int LOGNS, bool INV>
+template <class T, int LOGN, int LOGC, int LS, int LOGNS, bool INV, int EPT = 8>
 __device__ __forceinline__ void stage_fixed(cx<T>* s, const TwE<T>* __restrict__ tw, int tid) {
   constexpr int LR = wp_stage_radix_log(LOGN, LOGNS);
   constexpr int R = 1 << LR;
   constexpr int C = 1 << LOGC;
   constexpr int NR = 1 << (LOGN - LR);
-  constexpr int NT = (C << LOGN) / 8;
-  constexpr int B = 8 / R;
+  constexpr int NT = (C << LOGN) / EPT;  // threads: EPT elements each
+  constexpr int B = EPT / R;
   constexpr int NS = 1 << LOGNS;
   cx<T> v[B][R];
 #pragma unroll
@@ -336,11 +336,11 @@ __device__ __forceinline__ void stage_fixed(cx<T>* s, const TwE<T>* __restrict__
   __syncthreads();
 }
 
-template <class T, int LOGN, int LOGC, int LS, bool INV, int LOGNS>
+template <class T, int LOGN, int LOGC, int LS, bool INV, int LOGNS, int EPT = 8>
 __device__ __forceinline__ void fft_fixed(cx<T>* s, const TwE<T>* __restrict__ tw, int tid) {
   if constexpr (LOGNS < LOGN) {
-    stage_fixed<T, LOGN, LOGC, LS, LOGNS, INV>(s, tw + wp_stage_tw_offset(LOGN, LOGNS), tid);
-    fft_fixed<T, LOGN, LOGC, LS, INV, LOGNS + wp_stage_radix_log(LOGN, LOGNS)>(s, tw, tid);
+    stage_fixed<T, LOGN, LOGC, LS, LOGNS, INV, EPT>(s, tw + wp_stage_tw_offset(LOGN, LOGNS), tid);
+    fft_fixed<T, LOGN, LOGC, LS, INV, LOGNS + wp_stage_radix_log(LOGN, LOGNS), EPT>(s, tw, tid);
   }
 }
 
@@ -1234,12 +1234,40 @@ __global__ void __launch_bounds__(256) k_prep_batch(const PrepParams<T>* __restr
 // plane wave exp(-i (theta0 + j delta)) = hiT[j / 64] loT[j mod 64] (both tables formed
 // per step with FP64 sincos of directly computed arguments), and the remaining terms are
 // evaluated at every point. The FP64 product of the factors is applied to the state.
-template <class T, int E>
-__device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, double t, int half, double* fco,
-                                      cx<double>* hiT, cx<double>* loT, int tid, int nthr) {
+// Line shape of the resident kernel: Res1dDyn holds the length and block size at run
+// time (E elements per thread, run-time Stockham stages); Res1dFix<LOGN, EPT> makes them
+// compile-time constants (n = 2^LOGN, n / EPT threads, unrolled stages with per-stage
+// twiddle records, kinetic factors as records).
+template <int E>
+struct Res1dDyn {
+  static constexpr bool fixed = false;
+  int logn, n, nthr;
+  template <class T>
+  __device__ explicit Res1dDyn(const Res1dParams<T>& p) : logn(p.logn), n(1 << p.logn), nthr(p.nthreads) {}
+  template <class T, bool INV>
+  __device__ __forceinline__ void fft(cx<T>* s, const Res1dParams<T>& p, int tid) const {
+    fft_tile<T, E, INV>(s, logn, 0, 1, p.W, p.W_lo, tid, nthr);
+  }
+};
+
+template <int LOGN, int EPT>
+struct Res1dFix {
+  static constexpr bool fixed = true;
+  static constexpr int logn = LOGN, n = 1 << LOGN, nthr = (1 << LOGN) / EPT;
+  template <class T>
+  __device__ explicit Res1dFix(const Res1dParams<T>&) {}
+  template <class T, bool INV>
+  __device__ __forceinline__ void fft(cx<T>* s, const Res1dParams<T>& p, int tid) const {
+    fft_fixed<T, LOGN, 0, 1, INV, 0, EPT>(s, reinterpret_cast<const TwE<T>*>(p.Wst), tid);
+  }
+};
+
+template <class T, class RS>
+__device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, const RS& rs, double t, int half,
+                                      double* fco, cx<double>* hiT, cx<double>* loT, int tid) {
   const DevPot& pot = *p.pot;
   const double tau = half ? 0.5 * p.g.dt : p.g.dt;
-  const int n = 1 << p.logn;
+  const int n = rs.n, nthr = rs.nthr;
   __syncthreads();
   if (tid < pot.nterms) fco[tid] = term_coef(pot.term[tid], t);
   __syncthreads();
@@ -1295,25 +1323,31 @@ __device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, double 
   __syncthreads();
 }
 
-template <class T, int E>
-__device__ void res1d_kinetic(cx<T>* s, const Res1dParams<T>& p, const cx<T>* K, const cx<T>* Klo, int tid,
-                              int nthr) {
-  fft_tile<T, E, false>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
-  const int n = 1 << p.logn;
-  const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
-  for (int i = tid; i < n; i += nthr) s[i] = apply_factor(s[i], K[i], Klo[i], one, zero);
+template <class T, class RS>
+__device__ void res1d_kinetic(cx<T>* s, const Res1dParams<T>& p, const RS& rs, int half, int tid) {
+  rs.template fft<T, false>(s, p, tid);
+  if constexpr (RS::fixed) {
+    const TwE<T>* K = p.Krec[half];
+#pragma unroll
+    for (int i = tid; i < rs.n; i += rs.nthr) s[i] = tw_apply<false>(s[i], K[i]);
+  } else {
+    const cx<T>* K = half ? p.Khalf : p.Kfull;
+    const cx<T>* Klo = half ? p.Khalf_lo : p.Kfull_lo;
+    const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
+    for (int i = tid; i < rs.n; i += rs.nthr) s[i] = apply_factor(s[i], K[i], Klo[i], one, zero);
+  }
   __syncthreads();
-  fft_tile<T, E, true>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
+  rs.template fft<T, true>(s, p, tid);
 }
 
-template <class T, int E>
-__device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
+template <class T, class RS>
+__device__ void res1d_body(const Res1dParams<T>& p, const RS& rs, cx<T>* s) {
   __shared__ double red[32][NQ];
   __shared__ double qp[NQ], qm[NQ];
   __shared__ double fco[WP_MAX_TERMS];
   __shared__ cx<double> hiT[256], loT[64];  // plane-wave tables (n <= 16384)
-  const int tid = threadIdx.x, nthr = p.nthreads;
-  const int n = 1 << p.logn;
+  const int tid = threadIdx.x, nthr = rs.nthr;
+  const int n = rs.n;
   const int64_t s0 = p.ctrl->step;
   const double dt = p.g.dt;
   auto tim = [&](int64_t k) { return p.g.t0 + (double)k * dt; };
@@ -1324,17 +1358,17 @@ __device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
   const int64_t m = p.nsteps;
   if (m > 0) {
     if (p.order == WP_ORDER_VKV) {
-      res1d_potential_phase<T, E>(s, p, tim(s0), 1, fco, hiT, loT, tid, nthr);
+      res1d_potential_phase<T>(s, p, rs, tim(s0), 1, fco, hiT, loT, tid);
       for (int64_t k = 0; k < m; k++) {
-        res1d_kinetic<T, E>(s, p, p.Kfull, p.Kfull_lo, tid, nthr);
+        res1d_kinetic<T>(s, p, rs, 0, tid);
         const bool last = (k == m - 1);
-        res1d_potential_phase<T, E>(s, p, tim(s0 + k + 1), last ? 1 : 0, fco, hiT, loT, tid, nthr);
+        res1d_potential_phase<T>(s, p, rs, tim(s0 + k + 1), last ? 1 : 0, fco, hiT, loT, tid);
       }
     } else {
-      res1d_kinetic<T, E>(s, p, p.Khalf, p.Khalf_lo, tid, nthr);
+      res1d_kinetic<T>(s, p, rs, 1, tid);
       for (int64_t k = 0; k < m; k++) {
-        res1d_potential_phase<T, E>(s, p, tim(s0 + k) + 0.5 * dt, 0, fco, hiT, loT, tid, nthr);
-        res1d_kinetic<T, E>(s, p, (k == m - 1) ? p.Khalf : p.Kfull, (k == m - 1) ? p.Khalf_lo : p.Kfull_lo, tid, nthr);
+        res1d_potential_phase<T>(s, p, rs, tim(s0 + k) + 0.5 * dt, 0, fco, hiT, loT, tid);
+        res1d_kinetic<T>(s, p, rs, (k == m - 1) ? 1 : 0, tid);
       }
     }
   }
@@ -1371,7 +1405,7 @@ __device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
       }
     }
     block_sum(acc, qp, red);
-    fft_tile<T, E, false>(s, p.logn, 0, 1, p.W, p.W_lo, tid, nthr);
+    rs.template fft<T, false>(s, p, tid);
 #pragma unroll
     for (int q = 0; q < NQ; q++) acc[q] = 0.0;
     for (int i = tid; i < n; i += nthr) {
@@ -1398,13 +1432,20 @@ __device__ void res1d_body(const Res1dParams<T>& p, cx<T>* s) {
 template <class T, int E, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_res1d(const Res1dParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  res1d_body<T, E>(p, reinterpret_cast<cx<T>*>(smem_raw));
+  res1d_body<T>(p, Res1dDyn<E>(p), reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+// Fixed-length resident line: n = 2^LOGN, n / EPT threads.
+template <class T, int LOGN, int EPT>
+__global__ void __launch_bounds__((1 << LOGN) / EPT) k_res1d_fixed(const Res1dParams<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  res1d_body<T>(p, Res1dFix<LOGN, EPT>(p), reinterpret_cast<cx<T>*>(smem_raw));
 }
 
 // Batched resident lines: block b runs instance b (all of one line length) for nsteps.
-template <class T, int E, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_res1d_batch(const Res1dParams<T>* __restrict__ params, int64_t nsteps) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+template <class T, class RS>
+__device__ __forceinline__ void res1d_batch_body(const Res1dParams<T>* __restrict__ params, int64_t nsteps,
+                                                 cx<T>* s) {
   __shared__ __align__(16) unsigned char raw[sizeof(Res1dParams<T>)];
   Res1dParams<T>& p = *reinterpret_cast<Res1dParams<T>*>(raw);
   const int* src = reinterpret_cast<const int*>(&params[blockIdx.x]);
@@ -1416,7 +1457,20 @@ __global__ void __launch_bounds__(MAXT) k_res1d_batch(const Res1dParams<T>* __re
     p.obs = 0;
   }
   __syncthreads();
-  res1d_body<T, E>(p, reinterpret_cast<cx<T>*>(smem_raw));
+  res1d_body<T>(p, RS(p), s);
+}
+
+template <class T, int E, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_res1d_batch(const Res1dParams<T>* __restrict__ params, int64_t nsteps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  res1d_batch_body<T, Res1dDyn<E>>(params, nsteps, reinterpret_cast<cx<T>*>(smem_raw));
+}
+
+template <class T, int LOGN, int EPT>
+__global__ void __launch_bounds__((1 << LOGN) / EPT)
+    k_res1d_fixed_batch(const Res1dParams<T>* __restrict__ params, int64_t nsteps) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  res1d_batch_body<T, Res1dFix<LOGN, EPT>>(params, nsteps, reinterpret_cast<cx<T>*>(smem_raw));
 }
 
 #ifdef WP_COMMON_KERNELS

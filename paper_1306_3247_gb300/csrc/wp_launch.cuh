@@ -27,6 +27,7 @@ int res1d_smem_limit_set(size_t smem) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 8, 256>, (cudaFuncAttribute)a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 16, 512>, (cudaFuncAttribute)a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_res1d<T, 16, 1024>, (cudaFuncAttribute)a, (int)smem);
+  if (e == cudaSuccess) e = (cudaError_t)res1d_fixed_smem_limit_set<T>(smem);
   return cuda_status(e);
 }
 
@@ -73,6 +74,7 @@ int launch_prep(const PrepParams<T>& p, void* stream) {
 template <class T>
 int launch_res1d(const Res1dParams<T>& p, size_t smem, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
+  if (p.fixed) return launch_res1d_fixed<T>(p, smem, stream);
   if (p.ept == 8 && p.nthreads <= 256)
     k_res1d<T, 8, 256><<<1, p.nthreads, smem, st>>>(p);
   else if (p.ept == 16 && p.nthreads <= 512)

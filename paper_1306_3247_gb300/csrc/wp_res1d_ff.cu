@@ -1,0 +1,6 @@
+// Fixed-length resident-line kernels (1-D propagation) for the float-float complex128-accuracy form.
+#include <type_traits>
+
+#include "wp_res1d_launch.cuh"
+
+WP_RES1D_TU(ff)
