@@ -878,6 +878,13 @@ struct BatchClass1D {
   void* dparams = nullptr;
 };
 
+// Blocks off .. off + n - 1 of a pass's class-sorted block list: the instances whose pass
+// axis has 2^logn points (logn 6..10: fixed-size kernel; 0: run-time shape).
+struct BatchPassClass {
+  int logn = 0;
+  int64_t off = 0, n = 0;
+};
+
 struct wp_batch {
   int prec = WP_C128;
   cudaStream_t stream = nullptr;
@@ -899,6 +906,7 @@ struct wp_batch {
   cudaStream_t side = nullptr;  // second stream: the 1-D part runs beside the 2-D part
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t ntiles_z = 0, ntiles_x = 0;
+  std::vector<BatchPassClass> cls_z, cls_x;  // line-length classes of the two passes
   size_t smem2d = 0;
   std::map<int64_t, cudaGraphExec_t> graphs;
   std::map<int64_t, int> seen;  // chunk lengths run once without a graph
@@ -925,6 +933,8 @@ void batch_free_compiled(wp_batch* b) {
   b->d_binst_z = b->d_binst_x = nullptr;
   b->max_lines = 0;
   b->d_tiles_z = b->d_tiles_x = nullptr;
+  b->cls_z.clear();
+  b->cls_x.clear();
   for (auto& c : b->classes1d)
     if (c.dparams) cudaFree(c.dparams);
   b->classes1d.clear();
@@ -990,8 +1000,6 @@ wp_status batch_compile(wp_batch* b) {
       }
       pz.push_back(qz);
       px.push_back(qx);
-      tz.push_back(az);
-      tx.push_back(ax);
       az += h->plan[1].ntiles;
       ax += h->plan[0].ntiles;
       PrepParams<T> q{};
@@ -1007,6 +1015,30 @@ wp_status batch_compile(wp_batch* b) {
     }
     b->ntiles_z = az;
     b->ntiles_x = ax;
+    // block lists sorted by the pass axis's line length, one launch per class
+    std::vector<int> bz, bx;
+    auto order = [&](int axis, std::vector<int64_t>& ts, std::vector<int>& binst, std::vector<BatchPassClass>& cl) {
+      std::map<int, std::vector<int>> by;
+      for (size_t k = 0; k < b->idx2d.size(); k++) {
+        const int ln = b->inst[b->idx2d[k]]->g.ln[axis];
+        by[ln >= kFixedLogMin && ln <= kFixedLogMax ? ln : 0].push_back((int)k);
+      }
+      ts.assign(b->idx2d.size(), 0);
+      for (auto& kv : by) {
+        BatchPassClass c;
+        c.logn = kv.first;
+        c.off = (int64_t)binst.size();
+        for (int k : kv.second) {
+          ts[k] = (int64_t)binst.size();
+          const int64_t nt = b->inst[b->idx2d[k]]->plan[axis].ntiles;
+          for (int64_t t = 0; t < nt; t++) binst.push_back(k);
+        }
+        c.n = (int64_t)binst.size() - c.off;
+        cl.push_back(c);
+      }
+    };
+    order(1, tz, bz, b->cls_z);
+    order(0, tx, bx, b->cls_x);
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_z, pz.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_x, px.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_prep, pp.size() * sizeof(PrepParams<T>)));
@@ -1019,12 +1051,6 @@ wp_status batch_compile(wp_batch* b) {
     WP_CUDA(nullptr, cudaMemcpy(b->d_prep, pp.data(), pp.size() * sizeof(PrepParams<T>), cudaMemcpyHostToDevice));
     WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_z, tz.data(), tz.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
     WP_CUDA(nullptr, cudaMemcpy(b->d_tiles_x, tx.data(), tx.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
-    std::vector<int> bz((size_t)az), bx((size_t)ax);
-    for (size_t k = 0; k < b->idx2d.size(); k++) {
-      const wp_handle* h = b->inst[b->idx2d[k]];
-      for (int64_t t = 0; t < h->plan[1].ntiles; t++) bz[(size_t)(tz[k] + t)] = (int)k;
-      for (int64_t t = 0; t < h->plan[0].ntiles; t++) bx[(size_t)(tx[k] + t)] = (int)k;
-    }
     WP_CUDA(nullptr, cudaMalloc(&b->d_binst_z, bz.size() * sizeof(int)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_binst_x, bx.size() * sizeof(int)));
     WP_CUDA(nullptr, cudaMemcpy(b->d_binst_z, bz.data(), bz.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -1049,18 +1075,26 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
                      "batched line records");
   };
   auto zpass = [&](uint32_t f) -> wp_status {
-    b->launches++;
-    return launch_rc(nullptr,
-                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, b->d_binst_z, b->ntiles_z,
-                                          f, 0, b->smem2d, st),
-                     "batched pass");
+    for (const BatchPassClass& c : b->cls_z) {
+      b->launches++;
+      const wp_status r = launch_rc(nullptr,
+                                    launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, b->d_binst_z,
+                                                         c.logn, c.off, c.n, f, 0, b->smem2d, st),
+                                    "batched pass");
+      if (r != WP_OK) return r;
+    }
+    return WP_OK;
   };
   auto xpass = [&](int khalf) -> wp_status {
-    b->launches++;
-    return launch_rc(nullptr,
-                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, b->d_binst_x, b->ntiles_x,
-                                          F_KIN, khalf, b->smem2d, st),
-                     "batched pass");
+    for (const BatchPassClass& c : b->cls_x) {
+      b->launches++;
+      const wp_status r = launch_rc(nullptr,
+                                    launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, b->d_binst_x,
+                                                         c.logn, c.off, c.n, F_KIN, khalf, b->smem2d, st),
+                                    "batched pass");
+      if (r != WP_OK) return r;
+    }
+    return WP_OK;
   };
   wp_status s2;
   // the 1-D classes run on a side stream forked from, and joined back into, the batch

@@ -8,32 +8,53 @@
 namespace wp {
 namespace batch_detail {
 
-template <class T, bool CONTIG>
-int launch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t ntiles,
-           uint32_t flags, int khalf, size_t smem, void* stream) {
+template <class T, bool CONTIG, int LOGN>
+int launch_cls(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t block_off,
+               int64_t nblocks, uint32_t flags, int khalf, size_t smem, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_pass_batch<T, CONTIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    const cudaError_t e = cudaFuncSetAttribute(k_pass_batch<T, CONTIG, LOGN>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     if (e != cudaSuccess) return (int)e;
     attr = true;
   }
-  if (ntiles > 0)
-    k_pass_batch<T, CONTIG><<<(unsigned)ntiles, 256, smem, (cudaStream_t)stream>>>(params, tile_start, block_inst,
-                                                                                  flags, khalf);
+  if (nblocks > 0)
+    k_pass_batch<T, CONTIG, LOGN><<<(unsigned)nblocks, 256, smem, st>>>(params, tile_start, block_inst, block_off,
+                                                                        flags, khalf);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : (int)e;
+}
+
+// One launch for the class of line length 2^logn (6..10: fixed-size kernels; other: run-time shape).
+template <class T, bool CONTIG>
+int launch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int logn,
+           int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (logn) {
+    case 6:
+      return launch_cls<T, CONTIG, 6>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+    case 7:
+      return launch_cls<T, CONTIG, 7>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+    case 8:
+      return launch_cls<T, CONTIG, 8>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+    case 9:
+      return launch_cls<T, CONTIG, 9>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+    case 10:
+      return launch_cls<T, CONTIG, 10>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+    default:
+      return launch_cls<T, CONTIG, 0>(params, tile_start, block_inst, block_off, nblocks, flags, khalf, smem, st);
+  }
 }
 
 }  // namespace batch_detail
 }  // namespace wp
 
-#define WP_BATCH_TU(T, CONTIG, NAME)                                                                    \
-  namespace wp {                                                                                        \
-  template <>                                                                                           \
-  int NAME<T>(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst,            \
-              int64_t ntiles, uint32_t flags, int khalf, size_t smem, void* stream) {                   \
-    return batch_detail::launch<T, CONTIG>(params, tile_start, block_inst, ntiles, flags, khalf, smem,  \
-                                           stream);                                                     \
-  }                                                                                                     \
+#define WP_BATCH_TU(T, CONTIG, NAME)                                                                      \
+  namespace wp {                                                                                          \
+  template <>                                                                                             \
+  int NAME<T>(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int logn,   \
+              int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) { \
+    return batch_detail::launch<T, CONTIG>(params, tile_start, block_inst, logn, block_off, nblocks, flags, \
+                                           khalf, smem, stream);                                          \
+  }                                                                                                       \
   }

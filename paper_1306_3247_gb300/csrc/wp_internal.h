@@ -300,8 +300,8 @@ template <class T> int launch_convert(const ConvParams<T>& p, void* stream);
 template <class T> int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream);
 template <class T> int launch_lines(const LinesParams<T>& p, void* stream);
 // batched launches (one block range per instance)
-template <class T> int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start,
-                                         const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
+template <class T> int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst,
+                                         int logn, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf,
                                          size_t smem, void* stream);
 template <class T> int launch_lines_batch(const LinesParams<T>* params, int ninst, int64_t max_lines,
                                           void* stream);
@@ -317,13 +317,14 @@ template <class T> int pass_smem_limit_set(size_t smem);
 // fixed-size pass kernels (their own translation units, wp_fixed_*.cu)
 template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 template <class T> int fixed_smem_limit_set(size_t smem);
-// batched pass kernels, contiguous and strided axis (wp_batch_*.cu)
+// batched pass kernels, contiguous and strided axis (wp_batch_*.cu): one launch per
+// line-length class, blocks block_off .. block_off + nblocks - 1 of the class-sorted list
 template <class T> int launch_pass_batch_contig(const PassParams<T>* params, const int64_t* tile_start,
-                                                const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
-                                                size_t smem, void* stream);
+                                                const int* block_inst, int logn, int64_t block_off, int64_t nblocks,
+                                                uint32_t flags, int khalf, size_t smem, void* stream);
 template <class T> int launch_pass_batch_strided(const PassParams<T>* params, const int64_t* tile_start,
-                                                 const int* block_inst, int64_t ntiles, uint32_t flags, int khalf,
-                                                 size_t smem, void* stream);
+                                                 const int* block_inst, int logn, int64_t block_off, int64_t nblocks,
+                                                 uint32_t flags, int khalf, size_t smem, void* stream);
 template <class T> int launch_fixed_obs(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 template <class T> int fixed_obs_smem_limit_set(size_t smem);
 template <class T> int res1d_smem_limit_set(size_t smem);

@@ -1026,14 +1026,19 @@ __device__ __forceinline__ void batch_fixed(const PassParams<T>& p, cx<T>* s, in
   pass_compute<T, 8, false>(p, sh, s, tile);
 }
 
-template <class T, bool CONTIG>
+// Batched pass over the instances of one shape class: block b of the launch is block
+// block_off + b of the class-sorted block list, serving tile (block - tile_start[inst]) of
+// instance block_inst[block]. LOGN = 6..10: fixed-size tiles; LOGN = 0: run-time shape.
+template <class T, bool CONTIG, int LOGN>
 __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
                                                     const int64_t* __restrict__ tile_start,
-                                                    const int* __restrict__ block_inst, uint32_t flags, int khalf) {
+                                                    const int* __restrict__ block_inst, int64_t block_off,
+                                                    uint32_t flags, int khalf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
   PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
-  const int inst = block_inst[blockIdx.x];
+  const int64_t blk = block_off + blockIdx.x;
+  const int inst = block_inst[blk];
   const int* src = reinterpret_cast<const int*>(&params[inst]);
   for (int k = threadIdx.x; k < (int)(sizeof(PassParams<T>) / sizeof(int)); k += blockDim.x)
     reinterpret_cast<int*>(raw)[k] = src[k];
@@ -1050,37 +1055,22 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
     }
   }
   __syncthreads();
-  const int64_t tile = (int64_t)blockIdx.x - tile_start[inst];
+  const int64_t tile = blk - tile_start[inst];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  switch (p.logn) {
-    case 6:
-      batch_fixed<T, 6, CONTIG>(p, s, tile);
-      return;
-    case 7:
-      batch_fixed<T, 7, CONTIG>(p, s, tile);
-      return;
-    case 8:
-      batch_fixed<T, 8, CONTIG>(p, s, tile);
-      return;
-    case 9:
-      batch_fixed<T, 9, CONTIG>(p, s, tile);
-      return;
-    case 10:
-      batch_fixed<T, 10, CONTIG>(p, s, tile);
-      return;
-    default:
-      break;
+  if constexpr (LOGN > 0) {
+    batch_fixed<T, LOGN, CONTIG>(p, s, tile);
+  } else {
+    const DynShape sh(p);
+    int64_t o0, cb;
+    tile_origin(p, sh, tile, o0, cb);
+    const int C = 1 << sh.logC, ntot = C << sh.logn;
+    for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
+      const int i = e >> sh.logC, l = e & (C - 1);
+      s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
+    }
+    __syncthreads();
+    pass_compute<T, 8, false>(p, sh, s, tile);
   }
-  const DynShape sh(p);
-  int64_t o0, cb;
-  tile_origin(p, sh, tile, o0, cb);
-  const int C = 1 << sh.logC, ntot = C << sh.logn;
-  for (int e = threadIdx.x; e < ntot; e += sh.nthr) {
-    const int i = e >> sh.logC, l = e & (C - 1);
-    s[i * sh.LS + l] = p.in[tile_gidx(p, sh, o0, cb, i, l)];
-  }
-  __syncthreads();
-  pass_compute<T, 8, false>(p, sh, s, tile);
 }
 
 template <class T>

@@ -109,12 +109,14 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
 }
 
 template <class T>
-int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t ntiles,
-                      uint32_t flags, int khalf, size_t smem, void* stream) {
+int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int logn,
+                      int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) {
   // the contiguous pass carries the potential phase, the strided one the kinetic factor
   if ((flags & F_KIN) == 0)
-    return launch_pass_batch_contig<T>(params, tile_start, block_inst, ntiles, flags, khalf, smem, stream);
-  return launch_pass_batch_strided<T>(params, tile_start, block_inst, ntiles, flags, khalf, smem, stream);
+    return launch_pass_batch_contig<T>(params, tile_start, block_inst, logn, block_off, nblocks, flags, khalf, smem,
+                                       stream);
+  return launch_pass_batch_strided<T>(params, tile_start, block_inst, logn, block_off, nblocks, flags, khalf, smem,
+                                      stream);
 }
 
 template <class T>
@@ -165,8 +167,8 @@ int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, in
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
   template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
   template int launch_lines<T>(const LinesParams<T>&, void*);                    \
-  template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, const int*, int64_t, uint32_t, int, size_t, \
-                                    void*);                                      \
+  template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, const int*, int, int64_t, int64_t, uint32_t, \
+                                    int, size_t, void*);                         \
   template int launch_prep_batch<T>(const PrepParams<T>*, int, int, double, double, void*);                    \
   template int launch_lines_batch<T>(const LinesParams<T>*, int, int64_t, void*);                              \
   template int launch_res1d_batch<T>(const Res1dParams<T>*, int, int, int, int64_t, size_t, void*);
