@@ -79,8 +79,8 @@ struct wp_handle {
   int res_ept = 8;
   size_t res_smem = 0;
   bool res_fixed = false;          // 1-D line of compile-time length (k_res1d_fixed)
-  cx<double>* res_S = nullptr;     // 1-D static phase tables, 2 x n (dt, dt/2)
-  uint32_t res_plane_mask = 0, res_gen_mask = 0;
+  void* res_S = nullptr;           // 1-D static phase tables, 2 x n records (dt, dt/2)
+  uint32_t res_static_mask = 0, res_plane_mask = 0, res_gen_mask = 0;
   int64_t host_step = 0;
   int64_t launches = 0;
   bool profiling = false;
@@ -553,8 +553,9 @@ Res1dParams<T> res1d_params(wp_handle* h) {
   p.ctrl = h->ctrl;
   p.obs_out = h->obs_dev;
   p.obs_cap = h->obs_cap;
-  p.S[0] = h->res_S;
-  p.S[1] = h->res_S + h->n[0];
+  p.S[0] = (const TwE<T>*)h->res_S;
+  p.S[1] = (const TwE<T>*)h->res_S + h->n[0];
+  p.static_mask = h->res_static_mask;
   p.plane_mask = h->res_plane_mask;
   p.gen_mask = h->res_gen_mask;
   p.fixed = h->res_fixed ? 1 : 0;
@@ -567,6 +568,20 @@ Res1dParams<T> res1d_params(wp_handle* h) {
 // Classifies the terms of a 1-D potential by time dependence and rebuilds the static
 // phase tables: linear and constant terms form a plane wave; terms with a constant
 // coefficient (A = 0) and a fixed centre (v = 0) are static; the rest are general.
+template <class T>
+wp_status res1d_static_tables(wp_handle* h, uint32_t stat) {
+  StaticPhaseParams<T> sp{};
+  sp.g = h->g;
+  sp.n = h->n[0];
+  sp.pot = h->dpot;
+  sp.static_mask = stat;
+  sp.S[0] = (TwE<T>*)h->res_S;
+  sp.S[1] = (TwE<T>*)h->res_S + h->n[0];
+  const int rc = launch_static_phase<T>(sp, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "static phase kernel");
+  return WP_OK;
+}
+
 wp_status res1d_split_potential(wp_handle* h) {
   uint32_t stat = 0, plane = 0, gen = 0;
   for (int k = 0; k < h->hpot.nterms; k++) {
@@ -578,17 +593,11 @@ wp_status res1d_split_potential(wp_handle* h) {
     else
       gen |= 1u << k;
   }
-  StaticPhaseParams sp{};
-  sp.g = h->g;
-  sp.n = h->n[0];
-  sp.pot = h->dpot;
-  sp.static_mask = stat;
-  sp.S[0] = h->res_S;
-  sp.S[1] = h->res_S + h->n[0];
-  const int rc = launch_static_phase(sp, h->stream);
-  if (rc) return cuda_fail(h, (cudaError_t)rc, "static phase kernel");
+  const wp_status st = WP_DISPATCH(h, res1d_static_tables<T>(h, stat));
+  if (st != WP_OK) return st;
   // batched instances run on other streams: the tables are complete on return
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->res_static_mask = stat;
   h->res_plane_mask = plane;
   h->res_gen_mask = gen;
   return WP_OK;
@@ -1299,7 +1308,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
     if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
     h->plan[0] = make_plan(h, 0);
-    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)n * sizeof(cx<double>))) != cudaSuccess)
+    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)n * sizeof(TwE<double>))) != cudaSuccess)
       return bail(cuda_fail(h, e, "static phase allocation"));
     if ((st = res1d_split_potential(h)) != WP_OK) return bail(st);
   }

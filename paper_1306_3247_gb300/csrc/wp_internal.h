@@ -246,7 +246,8 @@ struct Res1dParams {
   // static terms as FP64 tables S[0] (phase length dt) and S[1] (dt/2); linear and
   // constant terms as a plane wave exp(-i (beta x - gamma) tau / hbar) built per step
   // from two short tables; the rest evaluated point by point.
-  const cx<double>* S[2];
+  const TwE<T>* S[2];
+  uint32_t static_mask;
   uint32_t plane_mask;
   uint32_t gen_mask;
   int32_t fixed;             // compile-time line length (k_res1d_fixed), n = 2^8 .. 2^14
@@ -254,13 +255,14 @@ struct Res1dParams {
   const TwE<T>* Krec[2];     // kinetic factors dt, dt/2 as records (fixed)
 };
 
-// FP64 static phase tables of a 1-D handle (k_static_phase).
+// Static phase tables of a 1-D handle (k_static_phase), formed in FP64 and stored as records.
+template <class T>
 struct StaticPhaseParams {
   Geom g;
   int64_t n;
   const DevPot* pot;
   uint32_t static_mask;
-  cx<double>* S[2];    // exp(-i V_s dt / hbar), exp(-i V_s (dt/2) / hbar)
+  TwE<T>* S[2];        // exp(-i V_s dt / hbar), exp(-i V_s (dt/2) / hbar)
 };
 
 struct ReduceParams {
@@ -310,7 +312,7 @@ template <class T> int launch_prep_batch(const PrepParams<T>* params, int ninst,
 template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept,
                                           int64_t nsteps, size_t smem, void* stream);
 int launch_reduce(const ReduceParams& p, void* stream);
-int launch_static_phase(const StaticPhaseParams& p, void* stream);
+template <class T> int launch_static_phase(const StaticPhaseParams<T>& p, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);

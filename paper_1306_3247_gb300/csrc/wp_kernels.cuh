@@ -1219,11 +1219,13 @@ __global__ void __launch_bounds__(256) k_prep_batch(const PrepParams<T>* __restr
 // One CTA holds one 1-D line in shared memory for a chunk of steps: the whole step
 // (potential phase, FFT, kinetic factor, inverse FFT) runs without touching HBM.
 // V(x,t) = sum_k f_k(t) s_k(x,t) split by time dependence (Eq. 9 applied with the terms of
-// Tab. 2): static terms come from the FP64 tables S (built once per potential), linear and
+// Tab. 2): static terms come from the tables S (built once per potential), linear and
 // constant terms sum to beta(t) x - gamma(t), whose phase at x_j = xmin + j dx is the
 // plane wave exp(-i (theta0 + j delta)) = hiT[j / 64] loT[j mod 64] (both tables formed
 // per step with FP64 sincos of directly computed arguments), and the remaining terms are
-// evaluated at every point. The FP64 product of the factors is applied to the state.
+// evaluated at every point in FP64. The factors are applied one after the other as
+// records (complex64: high and low parts), so that the per-point work of the common
+// potentials stays off the FP64 pipe.
 // Line shape of the resident kernel: Res1dDyn holds the length and block size at run
 // time (E elements per thread, run-time Stockham stages); Res1dFix<LOGN, EPT> makes them
 // compile-time constants (n = 2^LOGN, n / EPT threads, unrolled stages with per-stage
@@ -1254,7 +1256,7 @@ struct Res1dFix {
 
 template <class T, class RS>
 __device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, const RS& rs, double t, int half,
-                                      double* fco, cx<double>* hiT, cx<double>* loT, int tid) {
+                                      double* fco, TwE<T>* hiT, TwE<T>* loT, int tid) {
   const DevPot& pot = *p.pot;
   const double tau = half ? 0.5 * p.g.dt : p.g.dt;
   const int n = rs.n, nthr = rs.nthr;
@@ -1281,18 +1283,23 @@ __device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, const R
       double sn, cs;
       if (k < nhi) {
         sincos(-fma((double)(k << 6), del, th0), &sn, &cs);
-        hiT[k] = mk(cs, sn);
+        hiT[k] = make_rec<T>(cs, sn);
       } else {
         sincos(-(double)(k - nhi) * del, &sn, &cs);
-        loT[k - nhi] = mk(cs, sn);
+        loT[k - nhi] = make_rec<T>(cs, sn);
       }
     }
     __syncthreads();
   }
-  const cx<double>* S = p.S[half ? 1 : 0];
+  const TwE<T>* S = p.S[half ? 1 : 0];
+  const bool stat = p.static_mask != 0;
   for (int i = tid; i < n; i += nthr) {
-    cx<double> fac = S[i];
-    if (plane) fac = cmul(fac, cmul(hiT[i >> 6], loT[i & 63]));
+    cx<T> v = s[i];
+    if (stat) v = tw_apply<false>(v, S[i]);
+    if (plane) {
+      v = tw_apply<false>(v, hiT[i >> 6]);
+      v = tw_apply<false>(v, loT[i & 63]);
+    }
     if (p.gen_mask) {
       const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
       double V = 0.0;
@@ -1304,11 +1311,9 @@ __device__ void res1d_potential_phase(cx<T>* s, const Res1dParams<T>& p, const R
       }
       double sn, cs;
       sincos(-V * tau / p.g.hbar, &sn, &cs);
-      fac = cmul(fac, mk(cs, sn));
+      v = tw_apply<false>(v, make_rec<T>(cs, sn));
     }
-    const T hc = (T)fac.re, hs = (T)fac.im;
-    const cx<T> one = mk((T)1, (T)0), zero = mk((T)0, (T)0);
-    s[i] = apply_factor(s[i], mk(hc, hs), mk((T)(fac.re - (double)hc), (T)(fac.im - (double)hs)), one, zero);
+    s[i] = v;
   }
   __syncthreads();
 }
@@ -1335,7 +1340,7 @@ __device__ void res1d_body(const Res1dParams<T>& p, const RS& rs, cx<T>* s) {
   __shared__ double red[32][NQ];
   __shared__ double qp[NQ], qm[NQ];
   __shared__ double fco[WP_MAX_TERMS];
-  __shared__ cx<double> hiT[256], loT[64];  // plane-wave tables (n <= 16384)
+  __shared__ TwE<T> hiT[256], loT[64];  // plane-wave tables (n <= 16384)
   const int tid = threadIdx.x, nthr = rs.nthr;
   const int n = rs.n;
   const int64_t s0 = p.ctrl->step;
@@ -1432,6 +1437,29 @@ __global__ void __launch_bounds__((1 << LOGN) / EPT) k_res1d_fixed(const Res1dPa
   res1d_body<T>(p, Res1dFix<LOGN, EPT>(p), reinterpret_cast<cx<T>*>(smem_raw));
 }
 
+// Static phase tables: exp(-i V_s(x_j) tau / hbar) for tau = dt and dt/2, V_s the sum of
+// the static terms (time-independent coefficient and centre) of a 1-D potential, formed
+// in FP64 and stored as records of T.
+template <class T>
+__global__ void __launch_bounds__(256) k_static_phase(const StaticPhaseParams<T> p) {
+  const DevPot& pot = *p.pot;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
+    double V = 0.0;
+    for (int k = 0; k < pot.nterms; k++) {
+      if (!((p.static_mask >> k) & 1u)) continue;
+      const wp_pot_term& tm = pot.term[k];
+      const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, 0.0) : term_axis_part(tm, 0, x, 0.0);
+      V += term_coef(tm, 0.0) * sh;
+    }
+    double sn, cs;
+    sincos(-V * p.g.dt / p.g.hbar, &sn, &cs);
+    p.S[0][i] = make_rec<T>(cs, sn);
+    sincos(-V * (0.5 * p.g.dt) / p.g.hbar, &sn, &cs);
+    p.S[1][i] = make_rec<T>(cs, sn);
+  }
+}
+
 // Batched resident lines: block b runs instance b (all of one line length) for nsteps.
 template <class T, class RS>
 __device__ __forceinline__ void res1d_batch_body(const Res1dParams<T>* __restrict__ params, int64_t nsteps,
@@ -1464,28 +1492,6 @@ __global__ void __launch_bounds__((1 << LOGN) / EPT)
 }
 
 #ifdef WP_COMMON_KERNELS
-// ------------------------------------------------------------------ static phase tables
-// exp(-i V_s(x_j) tau / hbar) for tau = dt and dt/2, V_s the sum of the static terms
-// (time-independent coefficient and centre) of a 1-D potential, in FP64.
-__global__ void __launch_bounds__(256) k_static_phase(const StaticPhaseParams p) {
-  const DevPot& pot = *p.pot;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
-    const double x = p.g.xmin[0] + (double)i * p.g.dx[0];
-    double V = 0.0;
-    for (int k = 0; k < pot.nterms; k++) {
-      if (!((p.static_mask >> k) & 1u)) continue;
-      const wp_pot_term& tm = pot.term[k];
-      const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, 0.0) : term_axis_part(tm, 0, x, 0.0);
-      V += term_coef(tm, 0.0) * sh;
-    }
-    double sn, cs;
-    sincos(-V * p.g.dt / p.g.hbar, &sn, &cs);
-    p.S[0][i] = mk(cs, sn);
-    sincos(-V * (0.5 * p.g.dt) / p.g.hbar, &sn, &cs);
-    p.S[1][i] = mk(cs, sn);
-  }
-}
-
 // ------------------------------------------------------------------ reduction kernel
 // One block: sums the per-CTA partials in a fixed order and writes the observable record.
 __global__ void __launch_bounds__(256) k_reduce(const ReduceParams p) {

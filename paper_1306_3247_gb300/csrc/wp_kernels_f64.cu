@@ -12,13 +12,6 @@ int launch_reduce(const ReduceParams& p, void* stream) {
   return cuda_status(cudaGetLastError());
 }
 
-int launch_static_phase(const StaticPhaseParams& p, void* stream) {
-  int64_t blocks = (p.n + 255) / 256;
-  if (blocks > 1024) blocks = 1024;
-  k_static_phase<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
-  return cuda_status(cudaGetLastError());
-}
-
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream) {
   k_set_step<<<1, 1, 0, (cudaStream_t)stream>>>(ctrl, step);
   return cuda_status(cudaGetLastError());
