@@ -165,6 +165,46 @@ void* wp_state_ptr(wp_handle* h);
 int64_t wp_get_step_index(const wp_handle* h);
 wp_status wp_set_step_index(wp_handle* h, int64_t s);
 
+/* ---------------------------------------------------------------- schedules and autotuning
+ * The paper fixes what a step computes (Sec. 2.1), not how the transforms are scheduled;
+ * this part has no counterpart there. A schedule selects how the FFT passes are run:
+ *   tile_log       log2 of the elements of a multi-dimensional pass tile (lines x points
+ *                  held in shared memory): 10, 11 or 12;
+ *   ept            minimum elements per thread, 8 or 16 (raised to 16 when a tile or a
+ *                  1-D line needs it);
+ *   max_radix_log  largest butterfly of the run-time-shape kernels: 2 (radix 4) or 3
+ *                  (radix 8);
+ *   fixed          1: use the compile-time-shape kernels where the shape allows (passes
+ *                  of 64..1024 points with 2048-element tiles; 1-D lines of 256..16384
+ *                  points), 0: always the run-time-shape kernels.
+ * The default is {11, 8, 3, 1}. Every schedule computes the same step; results differ
+ * only by rounding order.
+ *
+ * wp_set_schedule rebuilds the handle's pass plans (WP_EUNSUPPORTED when the schedule
+ * does not fit the grid: too many threads or too much shared memory; the handle keeps its
+ * previous schedule). It synchronises the handle's stream and must not be called during
+ * stream capture.
+ *
+ * wp_autotune times every candidate schedule on the handle (`steps` steps each after one
+ * warm-up step, CUDA events on the handle's stream), on a device copy of the state that
+ * is put back afterwards together with the step index, applies the fastest, and stores it
+ * in a process-wide cache keyed by (precision, ndim, extents, order). wp_create applies a
+ * cached schedule to every later handle of the same key (batched and served instances
+ * included). best_ms is the best time per step; ncandidates counts the schedules timed.
+ * Allocates a temporary state copy (WP_ENOMEM if that fails). steps >= 1. */
+typedef struct {
+  int32_t tile_log;
+  int32_t ept;
+  int32_t max_radix_log;
+  int32_t fixed;
+} wp_schedule;
+
+wp_status wp_get_schedule(const wp_handle* h, wp_schedule* out);
+wp_status wp_set_schedule(wp_handle* h, const wp_schedule* s);
+wp_status wp_autotune(wp_handle* h, int32_t steps, wp_schedule* best, double* best_ms, int32_t* ncandidates);
+int64_t wp_autotune_cache_size(void);
+void wp_autotune_cache_clear(void);
+
 /* Kernel timing for measurement: while enabled, every launch is bracketed by CUDA
  * events on the handle's stream (CUDA-graph replay is off). wp_profile_read returns
  * the launch count and total milliseconds recorded for one kernel class (names as in

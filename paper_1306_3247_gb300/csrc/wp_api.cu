@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <mutex>
 #include <cmath>
@@ -24,6 +25,7 @@ constexpr int kTileLog = 11;  // target tile: 2048 elements (8 per thread, 256 t
 struct PassPlan {
   int axis = 0;
   int logn = 0, logC = 0, LS = 1, log_inner = 0, nthreads = 32, ept = 8;
+  int max_radix_log = 3;
   bool fixed = false;
   int64_t ntiles = 0;
   size_t smem = 0;
@@ -75,8 +77,11 @@ struct wp_handle {
   double* obs_dev = nullptr;
   int64_t obs_cap = 0;
   PassPlan plan[3];
+  wp_schedule sched{11, 8, 3, 1};  // current pass schedule
+  int64_t part_cap = 0;            // tiles the partial-sum buffers hold
   int res_nthreads = 32;
   int res_ept = 8;
+  int res_max_radix_log = 3;
   size_t res_smem = 0;
   bool res_fixed = false;          // 1-D line of compile-time length (k_res1d_fixed)
   void* res_S = nullptr;           // 1-D static phase tables, 2 x n records (dt, dt/2)
@@ -151,7 +156,10 @@ wp_status launch_rc(wp_handle* h, int rc, const char* what) {
   return WP_OK;
 }
 
-PassPlan make_plan(const wp_handle* h, int axis) {
+// Pass plan of one axis under schedule sc: tiles of 2^tile_log elements (C = 2^logC lines,
+// at most 64, of n points), at least sc.ept elements per thread (16 when the tile exceeds
+// 2048), the fixed-size kernel when allowed and the shape is one it covers.
+PassPlan make_plan(const wp_handle* h, int axis, const wp_schedule& sc) {
   PassPlan p;
   p.axis = axis;
   const int nd = h->ndim;
@@ -162,7 +170,7 @@ PassPlan make_plan(const wp_handle* h, int axis) {
   p.log_inner = log_inner;
   const bool contig = (axis == nd - 1);
   const int lines_log = contig ? log_outer : log_inner;
-  int logC = kTileLog - p.logn;
+  int logC = sc.tile_log - p.logn;
   if (logC < 0) logC = 0;
   if (logC > 6) logC = 6;
   if (logC > lines_log) logC = lines_log;
@@ -170,15 +178,16 @@ PassPlan make_plan(const wp_handle* h, int axis) {
   const int C = 1 << logC;
   p.LS = C;
   const int64_t tile = int64_t(C) << p.logn;
-  const int E = tile <= 2048 ? 8 : 16;
+  const int E = (tile > 2048 || sc.ept >= 16) ? 16 : 8;
   int64_t thr = tile / E;
   if (thr < 1) thr = 1;
   p.ept = E;
   p.nthreads = (int)((thr + 31) / 32 * 32);
   p.ntiles = h->N / tile;
   p.smem = (size_t)p.LS * ((size_t)1 << p.logn) * h->elem;
-  p.fixed = (p.logn >= kFixedLogMin && p.logn <= kFixedLogMax && p.logC == kTileLog - p.logn && p.nthreads == 256 &&
-             p.ept == 8);
+  p.max_radix_log = sc.max_radix_log;
+  p.fixed = sc.fixed && (p.logn >= kFixedLogMin && p.logn <= kFixedLogMax && p.logC == kTileLog - p.logn &&
+                         p.nthreads == 256 && p.ept == 8);
   return p;
 }
 
@@ -411,6 +420,7 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.W_lo = tb[axis].W_lo;
   p.Wst = tb[axis].Wst;
   p.fixed = pl.fixed ? 1 : 0;
+  p.max_radix_log = pl.max_radix_log;
   for (int d = 0; d < h->ndim; d++) {
     p.K[d] = khalf ? tb[d].Khalf : tb[d].Kfull;
     p.K_lo[d] = khalf ? tb[d].Khalf_lo : tb[d].Kfull_lo;
@@ -531,6 +541,85 @@ wp_status ensure_obs(wp_handle* h, int64_t cap) {
   return WP_OK;
 }
 
+// Validates schedule sc for the handle and installs its plans (the handle is unchanged
+// on failure). Multi-D: tile threads within the kernel variants' limits, tiles within
+// shared memory, partial-sum buffers grown to the tile count. 1-D: the fixed-length
+// kernel when allowed and the length is one it covers, else the run-time-length kernel
+// with sc.ept elements per thread (16 for lines longer than 2048 points).
+wp_status apply_schedule(wp_handle* h, const wp_schedule& sc) {
+  if ((sc.tile_log < 10 || sc.tile_log > 12) || (sc.ept != 8 && sc.ept != 16) ||
+      (sc.max_radix_log != 2 && sc.max_radix_log != 3) || (sc.fixed != 0 && sc.fixed != 1))
+    return fail(h, WP_EINVAL, "schedule field out of range");
+  if (h->ndim > 1) {
+    PassPlan pl[3];
+    int64_t maxtiles = 1;
+    for (int d = 0; d < h->ndim; d++) {
+      pl[d] = make_plan(h, d, sc);
+      const bool ok = (pl[d].ept == 8 && pl[d].nthreads <= 256) || (pl[d].ept == 16 && pl[d].nthreads <= 512);
+      if (!ok) return fail(h, WP_EUNSUPPORTED, "schedule: too many threads for a tile");
+      if (pl[d].smem > 180 * 1024) return fail(h, WP_EUNSUPPORTED, "schedule: tile exceeds shared memory");
+      maxtiles = std::max(maxtiles, pl[d].ntiles);
+    }
+    if (maxtiles > h->part_cap) {
+      WP_CUDA(h, cudaStreamSynchronize(h->stream));
+      double *pp = nullptr, *pm = nullptr;
+      cudaError_t e = cudaMalloc(&pp, (size_t)maxtiles * NQ * sizeof(double));
+      if (e == cudaSuccess) e = cudaMalloc(&pm, (size_t)maxtiles * NQ * sizeof(double));
+      if (e != cudaSuccess) {
+        if (pp) cudaFree(pp);
+        return cuda_fail(h, e, "partials allocation");
+      }
+      if (h->part_pos) cudaFree(h->part_pos);
+      if (h->part_mom) cudaFree(h->part_mom);
+      h->part_pos = pp;
+      h->part_mom = pm;
+      h->part_cap = maxtiles;
+    }
+    WP_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int d = 0; d < h->ndim; d++) h->plan[d] = pl[d];
+  } else {
+    const int64_t n = h->n[0];
+    const int ln = h->g.ln[0];
+    const bool fx = sc.fixed && ln >= kRes1dLogMin && ln <= (h->elem == 8 ? kRes1dLogMax : 13);
+    const int E = fx ? wp_res1d_fixed_ept(ln) : ((n > 2048 || sc.ept >= 16) ? 16 : 8);
+    const int64_t thr = std::max<int64_t>(1, n / E);
+    const int nthr = (int)((thr + 31) / 32 * 32);
+    const bool ok = fx || (E == 8 && nthr <= 256) || (E == 16 && nthr <= 1024);
+    if (!ok) return fail(h, WP_EUNSUPPORTED, "schedule: 1-D line too long for the variant");
+    if ((size_t)n * h->elem > 200 * 1024) return fail(h, WP_EUNSUPPORTED, "1-D line too long for shared memory");
+    WP_CUDA(h, cudaStreamSynchronize(h->stream));
+    h->res_fixed = fx;
+    h->res_ept = E;
+    h->res_nthreads = nthr;
+    h->res_max_radix_log = sc.max_radix_log;
+    h->res_smem = (size_t)n * h->elem;
+    h->plan[0] = make_plan(h, 0, sc);
+  }
+  h->sched = sc;
+  return WP_OK;
+}
+
+// Process-wide cache of tuned schedules, keyed by precision, order and extents.
+std::mutex g_tune_mu;
+std::map<std::array<int64_t, 5>, wp_schedule> g_tune_cache;
+
+std::array<int64_t, 5> tune_key(const wp_handle* h) {
+  return {(int64_t)h->prec * 8 + (int64_t)h->pb.order * 4 + h->ndim, h->n[0], h->n[1], h->n[2], 0};
+}
+
+bool tune_cache_get(const wp_handle* h, wp_schedule* out) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(tune_key(h));
+  if (it == g_tune_cache.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+void tune_cache_put(const wp_handle* h, const wp_schedule& sc) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[tune_key(h)] = sc;
+}
+
 template <class T>
 Res1dParams<T> res1d_params(wp_handle* h) {
   Res1dParams<T> p{};
@@ -559,6 +648,7 @@ Res1dParams<T> res1d_params(wp_handle* h) {
   p.plane_mask = h->res_plane_mask;
   p.gen_mask = h->res_gen_mask;
   p.fixed = h->res_fixed ? 1 : 0;
+  p.max_radix_log = h->res_max_radix_log;
   p.Wst = tb[0].Wst;
   p.Krec[0] = tb[0].Kfull_rec;
   p.Krec[1] = tb[0].Khalf_rec;
@@ -963,11 +1053,11 @@ bool batchable_2d(const wp_handle* h) {
 template <class T>
 wp_status batch_compile(wp_batch* b) {
   batch_free_compiled(b);
-  std::map<int, BatchClass1D> cls;
+  std::map<std::array<int, 4>, BatchClass1D> cls;  // line length and kernel variant
   for (int k = 0; k < (int)b->inst.size(); k++) {
     wp_handle* h = b->inst[k];
     if (h->ndim == 1) {
-      BatchClass1D& c = cls[h->g.ln[0]];
+      BatchClass1D& c = cls[{h->g.ln[0], h->res_fixed ? 1 : 0, h->res_ept, h->res_max_radix_log}];
       c.logn = h->g.ln[0];
       c.nthreads = h->res_nthreads;
       c.ept = h->res_ept;
@@ -1029,8 +1119,9 @@ wp_status batch_compile(wp_batch* b) {
     auto order = [&](int axis, std::vector<int64_t>& ts, std::vector<int>& binst, std::vector<BatchPassClass>& cl) {
       std::map<int, std::vector<int>> by;
       for (size_t k = 0; k < b->idx2d.size(); k++) {
-        const int ln = b->inst[b->idx2d[k]]->g.ln[axis];
-        by[ln >= kFixedLogMin && ln <= kFixedLogMax ? ln : 0].push_back((int)k);
+        const wp_handle* hk = b->inst[b->idx2d[k]];
+        // fixed-size class when the instance's schedule uses the fixed kernel, else run-time shape
+        by[hk->plan[axis].fixed ? hk->g.ln[axis] : 0].push_back((int)k);
       }
       ts.assign(b->idx2d.size(), 0);
       for (auto& kv : by) {
@@ -1267,13 +1358,6 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     return bail(cuda_fail(h, e, "potential copy"));
   st = WP_DISPATCH(h, alloc_tables<T>(h));
   if (st != WP_OK) return bail(st);
-  // plans
-  int64_t maxtiles = 1;
-  for (int d = 0; d < h->ndim; d++) {
-    h->plan[d] = make_plan(h, d);
-    if (h->plan[d].ntiles > maxtiles) maxtiles = h->plan[d].ntiles;
-    if (h->ndim > 1 && h->plan[d].smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "axis too long for one tile"));
-  }
   if (h->ndim > 1) {
     const size_t rec = h->prec == WP_C64 ? sizeof(LineRec<float>) : sizeof(LineRec<double>);
     h->nlines_phase = h->N / h->n[h->ndim - 1];
@@ -1285,30 +1369,17 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
         return bail(cuda_fail(h, e, "line-record allocation"));
     for (int k = 0; k < 2; k++)
       if ((st = WP_DISPATCH(h, run_lines<T>(h, false, k))) != WP_OK) return bail(st);
-    size_t mx = 0;
-    for (int d = 0; d < h->ndim; d++) mx = std::max(mx, h->plan[d].smem);
-    const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
-    if (mx > 180 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "tile exceeds shared memory"));
-    if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
-    if ((e = cudaMalloc(&h->part_pos, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
-      return bail(cuda_fail(h, e, "partials allocation"));
-    if ((e = cudaMalloc(&h->part_mom, (size_t)maxtiles * NQ * sizeof(double))) != cudaSuccess)
-      return bail(cuda_fail(h, e, "partials allocation"));
-  } else {
-    const int64_t n = h->n[0];
-    const int ln = h->g.ln[0];
-    h->res_fixed = ln >= kRes1dLogMin && ln <= (h->elem == 8 ? kRes1dLogMax : 13);
-    const int E = h->res_fixed ? wp_res1d_fixed_ept(ln) : (n <= 2048 ? 8 : 16);
-    const int64_t thr = std::max<int64_t>(1, n / E);
-    h->res_ept = E;
-    h->res_nthreads = (int)((thr + 31) / 32 * 32);
-    if (h->res_nthreads > 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long"));
-    h->res_smem = (size_t)n * h->elem;
-    if (h->res_smem > 200 * 1024) return bail(fail(h, WP_EUNSUPPORTED, "1-D line too long for shared memory"));
-    const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
-    if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
-    h->plan[0] = make_plan(h, 0);
-    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)n * sizeof(TwE<double>))) != cudaSuccess)
+  }
+  const int rc = WP_DISPATCH(h, ensure_smem_limits<T>());
+  if (rc) return bail(cuda_fail(h, (cudaError_t)rc, "shared-memory limit"));
+  if ((st = apply_schedule(h, h->sched)) != WP_OK) return bail(st);
+  {
+    // a schedule tuned for this shape earlier in the process
+    wp_schedule cached;
+    if (tune_cache_get(h, &cached)) apply_schedule(h, cached);
+  }
+  if (h->ndim == 1) {
+    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)h->n[0] * sizeof(TwE<double>))) != cudaSuccess)
       return bail(cuda_fail(h, e, "static phase allocation"));
     if ((st = res1d_split_potential(h)) != WP_OK) return bail(st);
   }
@@ -1433,6 +1504,102 @@ wp_status wp_run(wp_handle* h, int64_t nt, int64_t nprint, wp_obs* obs, int64_t*
 wp_status wp_fft(wp_handle* h, int sign) {
   if (!h || (sign != 1 && sign != -1)) return fail(h, WP_EINVAL, "sign must be +1 or -1");
   return WP_DISPATCH(h, fft_seq<T>(h, sign));
+}
+
+wp_status wp_get_schedule(const wp_handle* h, wp_schedule* out) {
+  if (!h || !out) return WP_EINVAL;
+  *out = h->sched;
+  return WP_OK;
+}
+
+wp_status wp_set_schedule(wp_handle* h, const wp_schedule* s) {
+  if (!h || !s) return fail(h, WP_EINVAL, "NULL argument");
+  return apply_schedule(h, *s);
+}
+
+wp_status wp_autotune(wp_handle* h, int32_t steps, wp_schedule* best, double* best_ms, int32_t* ncandidates) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  if (steps < 1) return fail(h, WP_EINVAL, "steps < 1");
+  std::vector<wp_schedule> cand;
+  cand.push_back(wp_schedule{11, 8, 3, 1});
+  if (h->ndim > 1) {
+    for (int tl = 10; tl <= 12; tl++)
+      for (int e : {8, 16})
+        for (int r : {2, 3}) cand.push_back(wp_schedule{tl, e, r, 0});
+  } else {
+    for (int e : {8, 16})
+      for (int r : {2, 3}) cand.push_back(wp_schedule{11, e, r, 0});
+  }
+  const wp_schedule start = h->sched;
+  const int64_t step0 = h->host_step;
+  const size_t bytes = (size_t)h->N * h->elem;
+  void* save = nullptr;
+  cudaError_t e = cudaMalloc(&save, bytes);
+  if (e != cudaSuccess) return cuda_fail(h, e, "autotune state copy");
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  wp_status st = WP_OK;
+  wp_schedule win = start;
+  double win_ms = -1.0;
+  int timed = 0;
+  auto restore = [&]() -> wp_status {
+    cudaError_t r = cudaMemcpyAsync(h->state, save, bytes, cudaMemcpyDeviceToDevice, h->stream);
+    if (r != cudaSuccess) return cuda_fail(h, r, "autotune restore");
+    return wp_set_step_index(h, step0);
+  };
+  if ((e = cudaEventCreate(&ev0)) != cudaSuccess || (e = cudaEventCreate(&ev1)) != cudaSuccess) {
+    st = cuda_fail(h, e, "autotune events");
+  } else if ((e = cudaMemcpyAsync(save, h->state, bytes, cudaMemcpyDeviceToDevice, h->stream)) != cudaSuccess) {
+    st = cuda_fail(h, e, "autotune state copy");
+  } else {
+    for (const wp_schedule& c : cand) {
+      if (apply_schedule(h, c) != WP_OK) continue;  // not applicable to this grid
+      if ((st = wp_step(h, 1)) != WP_OK) break;
+      if ((e = cudaEventRecord(ev0, h->stream)) != cudaSuccess) {
+        st = cuda_fail(h, e, "autotune event");
+        break;
+      }
+      if ((st = wp_step(h, steps)) != WP_OK) break;
+      if ((e = cudaEventRecord(ev1, h->stream)) != cudaSuccess || (e = cudaEventSynchronize(ev1)) != cudaSuccess) {
+        st = cuda_fail(h, e, "autotune event");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      const double per = (double)ms / (double)steps;
+      timed++;
+      if (win_ms < 0.0 || per < win_ms) {
+        win_ms = per;
+        win = c;
+      }
+      if ((st = restore()) != WP_OK) break;
+    }
+  }
+  if (st == WP_OK && timed > 0) {
+    st = apply_schedule(h, win);
+    if (st == WP_OK) tune_cache_put(h, win);
+  } else {
+    apply_schedule(h, start);
+  }
+  if (st == WP_OK) st = restore();
+  cudaStreamSynchronize(h->stream);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  cudaFree(save);
+  if (st != WP_OK) return st;
+  if (best) *best = win;
+  if (best_ms) *best_ms = win_ms;
+  if (ncandidates) *ncandidates = timed;
+  return WP_OK;
+}
+
+int64_t wp_autotune_cache_size(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int64_t)g_tune_cache.size();
+}
+
+void wp_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
 }
 
 void* wp_state_ptr(wp_handle* h) { return h ? h->state : nullptr; }

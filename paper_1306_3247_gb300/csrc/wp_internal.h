@@ -171,6 +171,7 @@ struct PassParams {
   const cx<T>* W_lo;
   const void* Wst;     // per-stage twiddle records of the pass axis
   int32_t fixed;       // use the fixed-size kernel (n = 2^logn, 2048-element tiles)
+  int32_t max_radix_log;  // largest butterfly of the run-time-shape kernel (2 or 3)
   const cx<T>* K[3];
   const cx<T>* K_lo[3];
   const cx<T>* P[3];
@@ -251,6 +252,7 @@ struct Res1dParams {
   uint32_t plane_mask;
   uint32_t gen_mask;
   int32_t fixed;             // compile-time line length (k_res1d_fixed), n = 2^8 .. 2^14
+  int32_t max_radix_log;     // largest butterfly of the run-time-length kernel (2 or 3)
   const void* Wst;           // per-stage twiddle records (fixed)
   const TwE<T>* Krec[2];     // kinetic factors dt, dt/2 as records (fixed)
 };

@@ -263,13 +263,15 @@ __device__ __forceinline__ void fft_stage(cx<T>* s, int logn, int logC, int LS, 
 }
 
 // Whole-line transform of every line of the tile (unnormalised).
+// maxr: log2 of the largest butterfly (3: radix 8 while at least 5 or exactly 3 factors of
+// two remain, then 4, then 2; 2: radix 4 then 2).
 template <class T, int E, bool INV>
 __device__ void fft_tile(cx<T>* s, int logn, int logC, int LS, const cx<T>* __restrict__ W,
-                         const cx<T>* __restrict__ Wl, int tid, int nthr) {
+                         const cx<T>* __restrict__ Wl, int tid, int nthr, int maxr = 3) {
   int logNs = 0;
   while (logNs < logn) {
     const int rem = logn - logNs;
-    if (E >= 8 && (rem >= 5 || rem == 3)) {
+    if (E >= 8 && maxr >= 3 && (rem >= 5 || rem == 3)) {
       fft_stage<T, 8, E, INV>(s, logn, logC, LS, logNs, W, Wl, tid, nthr);
       logNs += 3;
     } else if (E >= 4 && rem >= 2) {
@@ -613,7 +615,7 @@ struct FixShape {
 // per-stage twiddle tables.
 template <class T, int E, bool INV>
 __device__ __forceinline__ void tile_fft(cx<T>* s, const PassParams<T>& p, const DynShape& sh, int tid) {
-  fft_tile<T, E, INV>(s, sh.logn, sh.logC, sh.LS, p.W, p.W_lo, tid, sh.nthr);
+  fft_tile<T, E, INV>(s, sh.logn, sh.logC, sh.LS, p.W, p.W_lo, tid, sh.nthr, p.max_radix_log);
 }
 template <class T, int E, bool INV, int LOGN, bool CONTIG>
 __device__ __forceinline__ void tile_fft(cx<T>* s, const PassParams<T>& p, const FixShape<LOGN, CONTIG>&, int tid) {
@@ -1238,7 +1240,7 @@ struct Res1dDyn {
   __device__ explicit Res1dDyn(const Res1dParams<T>& p) : logn(p.logn), n(1 << p.logn), nthr(p.nthreads) {}
   template <class T, bool INV>
   __device__ __forceinline__ void fft(cx<T>* s, const Res1dParams<T>& p, int tid) const {
-    fft_tile<T, E, INV>(s, logn, 0, 1, p.W, p.W_lo, tid, nthr);
+    fft_tile<T, E, INV>(s, logn, 0, 1, p.W, p.W_lo, tid, nthr, p.max_radix_log);
   }
 };
 

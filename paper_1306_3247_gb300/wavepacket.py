@@ -57,6 +57,11 @@ OBS_DTYPE = np.dtype([(n, "<f8") for n in ("t", "norm", "x0", "x1", "x2", "p0", 
                                             "energy", "ekin", "epot", "autocorr")] + [("step", "<i8")])
 
 
+class WpSchedule(ctypes.Structure):
+    _fields_ = [("tile_log", ctypes.c_int32), ("ept", ctypes.c_int32), ("max_radix_log", ctypes.c_int32),
+                ("fixed", ctypes.c_int32)]
+
+
 class WavepacketError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{message} (status {status})")
@@ -102,6 +107,11 @@ def load_library(build_if_missing: bool = True):
         "wp_kernel_count": ([], ctypes.c_int),
         "wp_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
         "wp_launch_count": ([H], ctypes.c_int64),
+        "wp_get_schedule": ([H, P(WpSchedule)], ctypes.c_int),
+        "wp_set_schedule": ([H, P(WpSchedule)], ctypes.c_int),
+        "wp_autotune": ([H, ctypes.c_int32, P(WpSchedule), P(ctypes.c_double), P(ctypes.c_int32)], ctypes.c_int),
+        "wp_autotune_cache_size": ([], ctypes.c_int64),
+        "wp_autotune_cache_clear": ([], None),
         "wp_destroy": ([H], ctypes.c_int),
         "wp_last_error": ([H], ctypes.c_char_p),
         "wp_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -275,6 +285,42 @@ def wp_launch_count(h) -> int:
     return load_library().wp_launch_count(h)
 
 
+def _sched_dict(s: WpSchedule) -> dict:
+    return {"tile_log": s.tile_log, "ept": s.ept, "max_radix_log": s.max_radix_log, "fixed": s.fixed}
+
+
+def wp_get_schedule(h) -> dict:
+    lib = load_library()
+    s = WpSchedule()
+    _check(lib, h, lib.wp_get_schedule(h, ctypes.byref(s)))
+    return _sched_dict(s)
+
+
+def wp_set_schedule(h, sched: dict):
+    lib = load_library()
+    s = WpSchedule(int(sched["tile_log"]), int(sched["ept"]), int(sched["max_radix_log"]), int(sched["fixed"]))
+    _check(lib, h, lib.wp_set_schedule(h, ctypes.byref(s)))
+
+
+def wp_autotune(h, steps: int = 3):
+    """Times the candidate schedules, applies and caches the fastest; returns
+    (schedule dict, ms per step, number of schedules timed)."""
+    lib = load_library()
+    s = WpSchedule()
+    ms = ctypes.c_double(0.0)
+    nc = ctypes.c_int32(0)
+    _check(lib, h, lib.wp_autotune(h, int(steps), ctypes.byref(s), ctypes.byref(ms), ctypes.byref(nc)))
+    return _sched_dict(s), ms.value, nc.value
+
+
+def wp_autotune_cache_size() -> int:
+    return load_library().wp_autotune_cache_size()
+
+
+def wp_autotune_cache_clear():
+    load_library().wp_autotune_cache_clear()
+
+
 def wp_destroy(h):
     lib = load_library()
     lib.wp_destroy(h)
@@ -328,6 +374,18 @@ class Propagator:
 
     def set_potential(self, terms):
         wp_set_potential(self.h, make_potential(list(terms)))
+
+    @property
+    def schedule(self) -> dict:
+        return wp_get_schedule(self.h)
+
+    def set_schedule(self, **sched):
+        cur = wp_get_schedule(self.h)
+        cur.update(sched)
+        wp_set_schedule(self.h, cur)
+
+    def autotune(self, steps: int = 3):
+        return wp_autotune(self.h, steps)
 
     def init_gaussian(self, x0, p0, sigma):
         wp_init_gaussian(self.h, x0, p0, sigma)

@@ -45,3 +45,11 @@ def test_library_reports_static_metadata_without_gpu():
     assert k >= 5
     assert all(lib.wp_kernel_name(i) for i in range(k))
     assert lib.wp_status_string(0) == b"ok"
+
+
+def test_autotune_cache_calls_without_gpu():
+    lib = ctypes.CDLL(B.build())
+    lib.wp_autotune_cache_size.restype = ctypes.c_int64
+    lib.wp_autotune_cache_clear.restype = None
+    lib.wp_autotune_cache_clear()
+    assert lib.wp_autotune_cache_size() == 0
