@@ -45,6 +45,19 @@ METRIC = "grid-point·steps/s (256³ c128 plain vs batched c64) + served p50/p99
 UNIT = "grid-point·steps/s"
 FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate measured on this machine's GB300 (profiles/gb300_alu_rates.md)
 
+# DRAM bytes (read + write) per launch of each pass class on the 256^3 workload, from one
+# ncu capture of the current kernels (profiles/pass_kernels_256cube_all_forms.md). Valid
+# for grid 256 only; any other grid reports null.
+TRAFFIC_256 = {
+    "c128": {"pass_contig": 477993216, "pass_strided": 471788288, "pass_kinetic": 477475584},
+    "c64": {"pass_contig": 210435072, "pass_strided": 209457664, "pass_kinetic": 214526208},
+    "c128f": {"pass_contig": 478860032, "pass_strided": 471800832, "pass_kinetic": 477464832},
+}
+
+
+def traffic_of(grid, precision, kernel_class):
+    return TRAFFIC_256.get(precision, {}).get(kernel_class) if grid == 256 else None
+
 
 def peaks():
     try:
@@ -193,6 +206,10 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     stream = torch.cuda.Stream()
     P = WPK.Propagator(pb, terms, precision, stream=stream.cuda_stream)
     P.init_gaussian(**cfg["init"])
+    tuned = None
+    if args.autotune:
+        sched, ms, ncand = P.autotune(steps=2)
+        tuned = {"schedule": sched, "ms_per_step": ms, "schedules_timed": ncand}
     psi0_dev = torch.empty(P.shape, dtype=torch.complex128, device="cuda")
     P.get_state_device(psi0_dev)
     torch.cuda.synchronize()
@@ -233,7 +250,7 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     clk = clocks.stop() if clocks else None
     dev_ms = max_over_ranks(world, dev_ms)
     out = {"value": world * npts * nt * steps / (dev_ms / 1e3), "ms_per_job": dev_ms / steps, "launches": launches,
-           "clocks": clk, "final_norm": float(obs["norm"][-1])}
+           "clocks": clk, "final_norm": float(obs["norm"][-1]), "autotune": tuned}
     if with_e2e:
         job_e2e()
         torch.cuda.synchronize()
@@ -255,11 +272,23 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     return out
 
 
-def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset):
-    """The uneven-instance batch: all instances advance `chunk` steps per bench step."""
+def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, autotune=True):
+    """The uneven-instance batch: all instances advance `chunk` steps per bench step.
+    With autotune, one instance of every distinct shape is tuned first; the cached
+    schedules then apply to all instances of that shape."""
     import torch
     inst = W.batched_instances(count=count)
     pts = [math.prod(c["problem"]["n"][: c["problem"]["ndim"]]) for c in inst]
+    tuned = {}
+    if autotune:
+        for c in inst:
+            key = tuple(c["problem"]["n"][: c["problem"]["ndim"]])
+            if key in tuned:
+                continue
+            with WPK.Propagator(c["problem"], c["terms"], precision) as T:
+                T.init_gaussian(**c["init"])
+                sched, ms, ncand = T.autotune(steps=3)
+            tuned[key] = sched
     B = WPK.Batch(precision)
     for c in inst:
         k = B.add(c["problem"], c["terms"])
@@ -278,7 +307,8 @@ def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset):
     B.close()
     out = {"value": sum(pts) * chunk * steps / el, "instances": count, "points": int(sum(pts)),
            "steps_per_bench_step": chunk, "ms_per_bench_step": el / steps * 1e3, "graph_launches_issued": launches,
-           "n1d": sum(1 for c in inst if c["problem"]["ndim"] == 1), "finite": finite, "precision": precision}
+           "n1d": sum(1 for c in inst if c["problem"]["ndim"] == 1), "finite": finite, "precision": precision,
+           "autotuned_shapes": {"x".join(map(str, k)): v for k, v in tuned.items()}}
     # plain per-instance FP64 form on a subset of the same instances, one handle at a time
     sub = inst[:plain_subset]
     handles = []
@@ -316,11 +346,13 @@ def main():
     ap.add_argument("--precision", default="c128", choices=["c128", "c64", "c128f"])
     ap.add_argument("--grid", type=int, default=256, help="points per axis of the 3-D workload")
     ap.add_argument("--nt", type=int, default=200)
-    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=25, help="oracle steps of the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline only (no forms, batch, serving)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="run the default schedule instead of the autotuned one")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
@@ -343,14 +375,16 @@ def main():
     if args.precision == "c128":
         flops = pass_flops_per_point(logn, dom_name) * npts
         roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS,
+                "traffic": traffic_of(args.grid, args.precision, dom_name),
                 "peak_source": "FP64 FMA rate measured on the box (profiles/gb300_alu_rates.md)",
                 "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"],
                 "hbm_frac": 2 * npts * elem / avg_s / 1e9 / pk["hbm_gbs"]}
     else:
         achieved = 2 * npts * elem / avg_s / 1e9
         roof = {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": src,
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic_of(args.grid, args.precision, dom_name),
+                "peak_source": src,
                 "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"]}
     extra = {}
     if not args.no_extra and rank == 0:
@@ -362,12 +396,12 @@ def main():
             el = 8 if form == "c64" else 16
             r["roofline"] = {"bound": "hbm", "kernel": kd[0],
                              "achieved": 2 * npts * el / (kd[1]["avg_ms"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                             "unit": "GB/s"}
+                             "unit": "GB/s", "traffic": traffic_of(args.grid, form, kd[0])}
             r["roofline"]["frac"] = r["roofline"]["achieved"] / pk["hbm_gbs"]
             r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
             extra.setdefault("forms", {})[form] = r
         extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=3, warmup=3,
-                                         plain_subset=64)
+                                         plain_subset=64, autotune=args.autotune)
         extra["served"] = bench_served(WPK, args.serve_requests, "c64")
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -383,7 +417,8 @@ def main():
             "config": {"workload": f"3d_barrier_{args.grid}^3 {args.precision} VKV, {args.nt} steps per job, "
                                    f"observables every 20",
                        "grid": [args.grid] * 3, "dt": 0.002, "steps_per_job": args.nt, "parallelism": "replicas",
-                       "l2": "state larger than the 129 MB L2 (268 MB complex128), no flush needed"},
+                       "l2": "state larger than the 129 MB L2 (268 MB complex128), no flush needed",
+                       "schedule": head["autotune"]},
             "e2e": head["e2e"], "gpu_launches": int(head["launches"]), "roofline": roof,
             "kernels": head["kernels"], "clocks": head["clocks"], "cpu_baseline": cpu,
         }

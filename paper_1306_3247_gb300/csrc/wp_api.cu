@@ -85,6 +85,7 @@ struct wp_handle {
   size_t res_smem = 0;
   bool res_fixed = false;          // 1-D line of compile-time length (k_res1d_fixed)
   void* res_S = nullptr;           // 1-D static phase tables, 2 x n records (dt, dt/2)
+  void* gauss_tab = nullptr;       // per-axis factors of the initial Gaussian
   uint32_t res_static_mask = 0, res_plane_mask = 0, res_gen_mask = 0;
   int64_t host_step = 0;
   int64_t launches = 0;
@@ -932,6 +933,13 @@ wp_status gaussian_impl(wp_handle* h, const double* x0, const double* p0, const 
     if (d < h->ndim) pref /= sqrt(sigma[d]);
   }
   p.pref = pref;
+  p.nsum = 0;
+  for (int d = 0; d < h->ndim; d++) {
+    p.off[d] = p.nsum;
+    p.nsum += h->n[d];
+  }
+  if (!h->gauss_tab) WP_CUDA(h, cudaMalloc(&h->gauss_tab, (size_t)p.nsum * sizeof(cx<double>)));
+  p.tab = (cx<double>*)h->gauss_tab;
   {
     LaunchScope ls(h, K_AUX);
     wp_status st = launch_rc(h, launch_gaussian<T>(p, h->N, h->stream), "gaussian kernel");
@@ -1394,7 +1402,7 @@ wp_status wp_destroy(wp_handle* h) {
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
                   h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
-                  h->lines_kin[1], h->res_S};
+                  h->lines_kin[1], h->res_S, h->gauss_tab};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ep : h->pending) {

@@ -294,6 +294,9 @@ struct GaussParams {
   Geom g;
   double x0[3], p0[3], sigma[3];
   double pref;
+  cx<double>* tab;     // per-axis factors, axis d at tab + off[d] (k_gaussian_axes)
+  int64_t off[3];
+  int64_t nsum;        // sum of the extents
 };
 
 // Launchers (defined per precision in the kernel translation units).

@@ -1543,7 +1543,25 @@ __global__ void k_convert(const ConvParams<T> p) {
   }
 }
 
-// Normalised Gaussian packet of Sec. 4.2, evaluated in FP64.
+// Normalised Gaussian packet of Sec. 4.2: a product over the axes of
+// exp(-(x_d - x0_d)^2 / sigma_d^2) exp(i p0_d (x_d - x0_d) / hbar), times the normalisation.
+// k_gaussian_axes forms the per-axis factors in FP64 (the normalisation folded into axis
+// 0); k_gaussian multiplies them at every point.
+template <class T>
+__global__ void k_gaussian_axes(const GaussParams<T> p) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < p.nsum; k += (int64_t)gridDim.x * blockDim.x) {
+    int d = 0;
+    while (d + 1 < p.g.ndim && k >= p.off[d + 1]) d++;
+    const int64_t i = k - p.off[d];
+    const double u = p.g.xmin[d] + (double)i * p.g.dx[d] - p.x0[d];
+    double amp = exp(-u * u / (p.sigma[d] * p.sigma[d]));
+    if (d == 0) amp *= p.pref;
+    double sn, cs;
+    sincos(p.p0[d] * u / p.g.hbar, &sn, &cs);
+    p.tab[k] = mk(amp * cs, amp * sn);
+  }
+}
+
 template <class T>
 __global__ void k_gaussian(const GaussParams<T> p, int64_t ntotal) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1554,17 +1572,9 @@ __global__ void k_gaussian(const GaussParams<T> p, int64_t ntotal) {
     gi[d] = (int)(r & ((1 << p.g.ln[d]) - 1));
     r >>= p.g.ln[d];
   }
-  double re = p.pref, im = 0.0;
-  for (int d = 0; d < p.g.ndim; d++) {
-    const double u = p.g.xmin[d] + (double)gi[d] * p.g.dx[d] - p.x0[d];
-    const double amp = exp(-u * u / (p.sigma[d] * p.sigma[d]));
-    double sn, cs;
-    sincos(p.p0[d] * u / p.g.hbar, &sn, &cs);
-    const double nr = (re * cs - im * sn) * amp, ni = (re * sn + im * cs) * amp;
-    re = nr;
-    im = ni;
-  }
-  p.psi[idx] = mk((T)re, (T)im);
+  cx<double> v = p.tab[gi[0]];
+  for (int d = 1; d < p.g.ndim; d++) v = cmul(v, p.tab[p.off[d] + gi[d]]);
+  p.psi[idx] = mk((T)v.re, (T)v.im);
 }
 
 }  // namespace wp

@@ -103,6 +103,9 @@ int launch_convert(const ConvParams<T>& p, void* stream) {
 
 template <class T>
 int launch_gaussian(const GaussParams<T>& p, int64_t n, void* stream) {
+  int64_t ab = (p.nsum + 255) / 256;
+  if (ab > 96) ab = 96;
+  if (ab > 0) k_gaussian_axes<T><<<(unsigned)ab, 256, 0, (cudaStream_t)stream>>>(p);
   const int64_t blocks = (n + 255) / 256;
   if (blocks > 0) k_gaussian<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p, n);
   return cuda_status(cudaGetLastError());

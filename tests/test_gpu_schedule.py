@@ -143,3 +143,13 @@ def test_batched_1d_instances_follow_their_schedule():
             assert np.array_equal(B.get_state(k), alone[k])
     finally:
         B.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-14), ("c128f", 1e-13), ("c64", 1e-7)])
+def test_initial_gaussian_3d_matches_oracle(prec, tol):
+    pb, terms = PROBLEMS["3d"]
+    init = {"x0": [0.3, -0.4, 0.5], "p0": [1.0, -0.5, 2.0], "sigma": [0.9, 1.3, 1.1]}
+    ref = O.gaussian(pb, **init)
+    with WPK.Propagator(pb, terms, prec) as P:
+        P.init_gaussian(**init)
+        assert rel_l2(P.get_state(), ref) < tol
