@@ -107,7 +107,7 @@ struct Ctrl {
   double gphase[WP_MAX_GAUSS];   // f_g(t) tau / hbar for the Gaussian terms
   double gcoef[WP_MAX_GAUSS];    // f_g(t)
   int32_t err;                   // first error raised by a kernel (0 = none)
-  int32_t pad;
+  uint32_t prep_done;            // blocks of the current k_prep launch that have finished
 };
 
 // Potential descriptor as the kernels read it (same field meaning as wp_potential).

@@ -1146,23 +1146,31 @@ __global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
 // exp(-i A_d tau/hbar) (argument reduced by the FP64 sincos), and the Gaussian-term
 // factors; the Gaussian coefficients f_g(t) and f_g(t) tau/hbar go to the control block.
 template <class T>
-__device__ void prep_body(const PrepParams<T>& p) {
+__device__ void prep_body(const PrepParams<T>& p, int blk, int nblk) {
   __shared__ int64_t s_step;
   if (threadIdx.x == 0) s_step = p.ctrl->step + p.step_add;
   __syncthreads();
   const int64_t step = s_step;
   const double t = p.g.t0 + (double)step * p.g.dt + p.t_shift;
   const DevPot& pot = *p.pot;
-  for (int d = 0; d < p.g.ndim; d++) {
-    const AxisTab<T>& tb = p.tab[d];
-    for (int64_t i = threadIdx.x; i < p.n[d]; i += blockDim.x) {
+  __shared__ double fco[WP_MAX_TERMS];
+  if (threadIdx.x < pot.nterms) fco[threadIdx.x] = term_coef(pot.term[threadIdx.x], t);
+  __syncthreads();
+  // one flat range over the entries of all axes, so that short axes share a round
+  const int64_t n01 = p.n[0] + (p.g.ndim > 1 ? p.n[1] : 0);
+  const int64_t nall = n01 + (p.g.ndim > 2 ? p.n[2] : 0);
+  for (int64_t e = blk * (int64_t)blockDim.x + threadIdx.x; e < nall; e += (int64_t)nblk * blockDim.x) {
+    {
+      const int d = e < p.n[0] ? 0 : (e < n01 ? 1 : 2);
+      const int64_t i = e - (d == 0 ? 0 : (d == 1 ? p.n[0] : n01));
+      const AxisTab<T>& tb = p.tab[d];
       const double x = p.g.xmin[d] + (double)i * p.g.dx[d];
       double A = 0.0;
       for (int k = 0; k < pot.nterms; k++) {
         const wp_pot_term& tm = pot.term[k];
         if (tm.shape == WP_SHAPE_GAUSS) continue;
         const double part = term_axis_part(tm, d, x, t);
-        if (part != 0.0) A += term_coef(tm, t) * part;
+        if (part != 0.0) A += fco[k] * part;
       }
       tb.A[i] = A;
       if (tb.AT) tb.AT[i] = (T)A;
@@ -1179,7 +1187,20 @@ __device__ void prep_body(const PrepParams<T>& p) {
       }
     }
   }
+  // The last block to finish publishes the Gaussian coefficients, the table time and the
+  // new step index: every block has read the old index before it counts itself done.
+  __shared__ bool s_last;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    if (nblk == 1) {
+      s_last = true;
+    } else {
+      __threadfence();
+      s_last = atomicAdd(&p.ctrl->prep_done, 1u) == (unsigned)(nblk - 1);
+    }
+  }
+  __syncthreads();
+  if (s_last && threadIdx.x == 0) {
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) {
       double fc = 0.0;
       if (gg < pot.ngauss) fc = term_coef(pot.term[pot.gauss_term[gg]], t);
@@ -1187,14 +1208,14 @@ __device__ void prep_body(const PrepParams<T>& p) {
       p.ctrl->gphase[gg] = fc * p.tau / p.g.hbar;
     }
     p.ctrl->t_tab = t;
+    p.ctrl->step = step;
+    if (nblk > 1) p.ctrl->prep_done = 0u;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) p.ctrl->step = step;
 }
 
 template <class T>
-__global__ void __launch_bounds__(1024) k_prep(const PrepParams<T> p) {
-  prep_body<T>(p);
+__global__ void __launch_bounds__(64) k_prep(const PrepParams<T> p) {
+  prep_body<T>(p, blockIdx.x, gridDim.x);
 }
 
 // Batched tables: block b updates instance b. The step increment, the time shift and the
@@ -1214,7 +1235,7 @@ __global__ void __launch_bounds__(256) k_prep_batch(const PrepParams<T>* __restr
     p.tau = tau_dt * p.g.dt;
   }
   __syncthreads();
-  prep_body<T>(p);
+  prep_body<T>(p, 0, 1);
 }
 
 // ------------------------------------------------------------------ 1-D resident kernel

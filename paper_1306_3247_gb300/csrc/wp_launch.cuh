@@ -66,7 +66,13 @@ int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* strea
 
 template <class T>
 int launch_prep(const PrepParams<T>& p, void* stream) {
-  k_prep<T><<<1, 1024, 0, (cudaStream_t)stream>>>(p);
+  // 64-thread blocks over the entries of all axes: the FP64 work spreads over SMs
+  int64_t nall = 0;
+  for (int d = 0; d < p.g.ndim; d++) nall += p.n[d];
+  int64_t blocks = (nall + 63) / 64;
+  if (blocks < 1) blocks = 1;
+  if (blocks > 512) blocks = 512;
+  k_prep<T><<<(unsigned)blocks, 64, 0, (cudaStream_t)stream>>>(p);
   return cuda_status(cudaGetLastError());
 }
 
