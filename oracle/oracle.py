@@ -31,7 +31,8 @@ class _Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("n", ctypes.c_int64 * 3), ("xmin", ctypes.c_double * 3),
                 ("L", ctypes.c_double * 3), ("mass", ctypes.c_double),
-                ("hbar", ctypes.c_double), ("dt", ctypes.c_double), ("t0", ctypes.c_double)]
+                ("hbar", ctypes.c_double), ("dt", ctypes.c_double), ("t0", ctypes.c_double),
+                ("vgrid", ctypes.c_void_p)]
 
 
 class _Term(ctypes.Structure):
@@ -89,6 +90,11 @@ def _problem(pb: dict) -> _Problem:
     p.hbar = float(pb.get("hbar", 1.0))
     p.dt = float(pb["dt"])
     p.t0 = float(pb.get("t0", 0.0))
+    vg = pb.get("vgrid")
+    if vg is not None:
+        arr = np.ascontiguousarray(np.asarray(vg, dtype=np.float64).reshape(_shape(pb)))
+        p._vgrid_keep = arr  # the array lives as long as the struct
+        p.vgrid = arr.ctypes.data
     return p
 
 

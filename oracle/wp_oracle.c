@@ -8,7 +8,9 @@
  * It shares no code, header, table or constant with the CUDA library.
  *
  * What it computes, and where each piece comes from:
- *   - Eq. (1)-(2): i hbar dpsi/dt = (P^2/2m + V(x,t)) psi.
+ *   - Eq. (1)-(2): i hbar dpsi/dt = (P^2/2m + V(x,t)) psi, V the sum of the
+ *     potential terms plus an optional static grid (Sec. 3.2.3: the user
+ *     potential() evaluated at every grid point).
  *   - Eq. (grid): x_i = x_min + i dx. This oracle uses the half-open periodic
  *     reading dx = L/n (the FFT period is n dx under either reading).
  *   - Eq. (ft) and the momentum grid of Sec. 2.1: the kinetic factor is applied
@@ -50,6 +52,8 @@ typedef struct {
   double xmin[3];      /* first grid point per axis */
   double L[3];         /* period per axis; dx = L/n */
   double mass, hbar, dt, t0;
+  const double *vgrid; /* optional static potential on the grid, row-major, or NULL:
+                          the user potential() of Sec. 3.2.3 evaluated once */
 } orc_problem;
 
 /* One potential term: V_term(x,t) = f(t) * shape(x,t).
@@ -225,7 +229,8 @@ void orc_potential_grid(const orc_problem *p, int32_t nterms, const orc_term *te
       for (int64_t k = 0; k < n2; k++) {
         double x[3] = {coord(p, 0, i), p->ndim > 1 ? coord(p, 1, j) : 0.0,
                        p->ndim > 2 ? coord(p, 2, k) : 0.0};
-        out[(i * n1 + j) * n2 + k] = orc_potential_at(p, nterms, terms, x, t);
+        int64_t idx = (i * n1 + j) * n2 + k;
+        out[idx] = orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0);
       }
 }
 
@@ -239,8 +244,9 @@ static void apply_potential_phase(const orc_problem *p, int32_t nterms, const or
       for (int64_t k = 0; k < n2; k++) {
         double x[3] = {coord(p, 0, i), p->ndim > 1 ? coord(p, 1, j) : 0.0,
                        p->ndim > 2 ? coord(p, 2, k) : 0.0};
-        double th = -orc_potential_at(p, nterms, terms, x, t) * tau / p->hbar;
         int64_t idx = (i * n1 + j) * n2 + k;
+        double v = orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0);
+        double th = -v * tau / p->hbar;
         psi[idx] = psi[idx] * CMPLX(cos(th), sin(th));
       }
 }
@@ -322,7 +328,7 @@ void orc_observe(const orc_problem *p, int32_t nterms, const orc_term *terms, co
           sx[d] += x[d] * rho;
           sxx[d] += x[d] * x[d] * rho;
         }
-        sv += orc_potential_at(p, nterms, terms, x, t) * rho;
+        sv += (orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0)) * rho;
         if (psi0) {
           cplx c = conj(psi0[idx]) * psi[idx];
           acr += creal(c);

@@ -38,10 +38,14 @@ MUTANTS = {
                              "double u = x[d] - (tm->c0[d] - tm->v[d] * t);\n        r += 0.5"),
     "y_axis_takes_x_index": ("double x[3] = {coord(p, 0, i), p->ndim > 1 ? coord(p, 1, j) : 0.0,\n"
                              "                       p->ndim > 2 ? coord(p, 2, k) : 0.0};\n"
-                             "        double th",
+                             "        int64_t idx = (i * n1 + j) * n2 + k;\n        double v",
                              "double x[3] = {coord(p, 0, i), p->ndim > 1 ? coord(p, 1, i) : 0.0,\n"
                              "                       p->ndim > 2 ? coord(p, 2, k) : 0.0};\n"
-                             "        double th"),
+                             "        int64_t idx = (i * n1 + j) * n2 + k;\n        double v"),
+    "grid_dropped_in_phase": ("double v = orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0);",
+                              "double v = orc_potential_at(p, nterms, terms, x, t);"),
+    "grid_dropped_in_energy": ("sv += (orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0)) * rho;",
+                               "sv += orc_potential_at(p, nterms, terms, x, t) * rho;"),
 }
 
 PIN_TESTS = [
@@ -54,6 +58,8 @@ PIN_TESTS = [
     lambda: PINS.test_driven_trap_1d_follows_verlet_map("kvk"),
     lambda: PINS.test_laser_trap_2d_follows_verlet_map_per_axis(),
     lambda: PINS.test_potential_terms_pointwise(),
+    lambda: PINS.test_constant_grid_potential_is_a_global_phase("vkv"),
+    lambda: PINS.test_harmonic_grid_potential_ground_state_3d(),
 ]
 
 

@@ -375,3 +375,53 @@ def test_paul_trap_3d_moments_follow_verlet_map():
                 r = obs[(s + 1) // npr]
                 assert abs(r[2 + d] - x) < 1e-12 * abs(x) and abs(r[5 + d] - p) < 1e-12 * 1e-27
     assert np.max(np.abs(obs[:, 1] - 1.0)) < 1e-12
+
+
+# --------------------------------------------------------------------------- static grid potential
+# Sec. 3.2.3: the user potential() gives V at every grid point; a static grid is that
+# function evaluated once and added to the analytic terms.
+@pytest.mark.parametrize("order", ["vkv", "kvk"])
+def test_constant_grid_potential_is_a_global_phase(order):
+    # V = c everywhere: exact solution = free evolution times exp(-i c t / hbar)
+    c, hbar, m = 0.37, 0.8, 1.3
+    pb = {"ndim": 1, "n": [1024], "xmin": [-20.0], "L": [40.0], "mass": m, "hbar": hbar,
+          "dt": 0.01, "t0": 0.0, "order": order}
+    psi0 = O.gaussian(pb, [-5.0], [2.0], [1.0])
+    psi = O.propagate(dict(pb, vgrid=np.full(1024, c)), [], psi0, 100)
+    x = grid(pb, 0)
+    ref = free_gaussian_1d(x, 1.0, -5.0, 2.0, 1.0, m, hbar) * np.exp(-1j * c * 1.0 / hbar)
+    assert rel_l2(psi, ref) < 1e-12
+
+
+def test_harmonic_grid_potential_ground_state_3d():
+    # V(x) = sum_d w_d^2 x_d^2 / 2 given as a grid: the anisotropic ground state has
+    # E = hbar sum w_d / 2 and <x_d^2> = sigma_d^2 / 4, and stays stationary
+    w = [1.0, 2.0, 0.5]
+    pb = {"ndim": 3, "n": [32, 32, 32], "xmin": [-8.0, -6.0, -12.0], "L": [16.0, 12.0, 24.0],
+          "mass": 1.0, "hbar": 1.0, "dt": 0.01, "t0": 0.0, "order": "vkv"}
+    X = np.meshgrid(*[grid(pb, d) for d in range(3)], indexing="ij")
+    V = sum(0.5 * w[d] ** 2 * X[d] ** 2 for d in range(3))
+    pg = dict(pb, vgrid=V)
+    sg = [math.sqrt(2.0 / ww) for ww in w]
+    psi0 = O.gaussian(pb, [0.0] * 3, [0.0] * 3, sg)
+    rec = O.observe(pg, [], psi0)
+    assert abs(rec[11] - sum(w) / 2) < 1e-11
+    assert abs(rec[13] - sum(w) / 4) < 1e-11
+    psi, obs = O.run(pg, [], psi0, 40, 20)
+    assert np.max(np.abs(np.abs(psi) ** 2 - np.abs(psi0) ** 2)) < 1e-4
+    assert np.max(np.abs(obs[:, 11] - sum(w) / 2)) < 1e-4
+
+
+def test_grid_adds_to_the_terms():
+    # the grid and the terms sum: half a trap as a term plus half as a grid equals the trap
+    pb = {"ndim": 2, "n": [32, 64], "xmin": [-6.0, -8.0], "L": [12.0, 16.0], "mass": 1.0, "hbar": 1.0,
+          "dt": 0.02, "t0": 0.3, "order": "kvk"}
+    full = [{"shape": "quad", "a": [1.0, 0.5], "coef": {"A0": 1.0}},
+            {"shape": "linear", "a": [0.3, 0.0], "coef": {"A": 1.0, "omega": 1.1}}]
+    half = [{"shape": "quad", "a": [1.0, 0.5], "coef": {"A0": 0.5}}, full[1]]
+    X = np.meshgrid(grid(pb, 0), grid(pb, 1), indexing="ij")
+    V = 0.25 * (1.0 * X[0] ** 2 + 0.5 * X[1] ** 2)
+    psi0 = W.random_state((32, 64), seed=2)
+    a = O.propagate(pb, full, psi0, 15)
+    b = O.propagate(dict(pb, vgrid=V), half, psi0, 15)
+    assert rel_l2(b, a) < 1e-13
