@@ -127,6 +127,24 @@ wp_status wp_create(const wp_problem* problem, void* stream, wp_handle** out);
 /* Set the potential (Sec. 3.2.2-3.2.3). Copied; may be called again between steps. */
 wp_status wp_set_potential(wp_handle* h, const wp_potential* pot);
 
+/* A static potential given on the grid: the user potential() of Sec. 3.2.3 evaluated
+ * once at every grid point. V holds n[0]*n[1]*n[2] FP64 energies in the state's layout
+ * (row-major, last axis fastest), a host pointer (on_device = 0) or a device pointer
+ * (on_device = 1); it is copied, and added to the analytic terms at every step and in
+ * the potential energy. V = NULL removes the grid. Device memory: 8 bytes per point, plus
+ * two 16-byte phase records per point for 2-D and 3-D grids (WP_ENOMEM if that fails).
+ * A handle with a grid is run on its own sequence inside a batch (not in the batched
+ * 2-D passes). Synchronises the handle's stream. */
+wp_status wp_set_potential_grid(wp_handle* h, const double* V, int on_device);
+
+/* The same grid from CUDA C source compiled at run time (NVRTC) for this GPU. src must
+ * define
+ *     __device__ double wp_user_potential(double x, double y, double z)
+ * (unused coordinates are 0); it is evaluated once at every grid point in FP64 and the
+ * result installed as by wp_set_potential_grid. A compilation error returns WP_EINVAL
+ * with the compiler log in wp_last_error. */
+wp_status wp_set_potential_source(wp_handle* h, const char* src);
+
 /* Copy a complex128 row-major psi into the state (Sec. 3.2.4 initialize_wf).
  * on_device = 0: psi is host memory; 1: device memory. The step index is kept. */
 wp_status wp_set_state(wp_handle* h, const void* psi, int on_device);

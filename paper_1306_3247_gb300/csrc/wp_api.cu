@@ -86,6 +86,9 @@ struct wp_handle {
   bool res_fixed = false;          // 1-D line of compile-time length (k_res1d_fixed)
   void* res_S = nullptr;           // 1-D static phase tables, 2 x n records (dt, dt/2)
   void* gauss_tab = nullptr;       // per-axis factors of the initial Gaussian
+  double* vgrid = nullptr;         // static grid potential (FP64, N values), or NULL
+  void* vgrid_rec[2] = {nullptr, nullptr};  // its phase records for dt, dt/2 (2-D, 3-D)
+  int phase_half = -1;             // tau of the current tables: 0 dt, 1 dt/2, -1 none
   uint32_t res_static_mask = 0, res_plane_mask = 0, res_gen_mask = 0;
   int64_t host_step = 0;
   int64_t launches = 0;
@@ -448,6 +451,8 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.Ox = tb[axis].Ox;
   p.Ok = tb[axis].Ok;
   p.AT = tb[axis].AT;
+  p.grid_v = h->vgrid;
+  p.grid_rec = (h->vgrid && h->phase_half >= 0) ? (const TwE<T>*)h->vgrid_rec[h->phase_half] : nullptr;
   return p;
 }
 
@@ -518,6 +523,7 @@ wp_status run_prep(wp_handle* h, int step_add, double t_shift, double tau, bool 
   p.step_add = step_add;
   p.t_shift = t_shift;
   p.tau = tau;
+  h->phase_half = tau == h->pb.dt ? 0 : (tau == 0.5 * h->pb.dt ? 1 : -1);
   {
     LaunchScope ls(h, K_PREP);
     wp_status st = launch_rc(h, launch_prep<T>(p, h->stream), "prep kernel");
@@ -622,6 +628,20 @@ void tune_cache_put(const wp_handle* h, const wp_schedule& sc) {
 }
 
 template <class T>
+wp_status grid_phase_tables(wp_handle* h) {
+  GridPhaseParams<T> gp{};
+  gp.V = h->vgrid;
+  gp.n = h->N;
+  gp.dt = h->pb.dt;
+  gp.hbar = h->pb.hbar;
+  gp.rec[0] = (TwE<T>*)h->vgrid_rec[0];
+  gp.rec[1] = (TwE<T>*)h->vgrid_rec[1];
+  const int rc = launch_grid_phase<T>(gp, h->stream);
+  if (rc) return cuda_fail(h, (cudaError_t)rc, "grid phase kernel");
+  return WP_OK;
+}
+
+template <class T>
 Res1dParams<T> res1d_params(wp_handle* h) {
   Res1dParams<T> p{};
   AxisTab<T>* tb = tabs<T>(h);
@@ -648,6 +668,7 @@ Res1dParams<T> res1d_params(wp_handle* h) {
   p.static_mask = h->res_static_mask;
   p.plane_mask = h->res_plane_mask;
   p.gen_mask = h->res_gen_mask;
+  p.vgrid = h->vgrid;
   p.fixed = h->res_fixed ? 1 : 0;
   p.max_radix_log = h->res_max_radix_log;
   p.Wst = tb[0].Wst;
@@ -666,6 +687,7 @@ wp_status res1d_static_tables(wp_handle* h, uint32_t stat) {
   sp.n = h->n[0];
   sp.pot = h->dpot;
   sp.static_mask = stat;
+  sp.vgrid = h->vgrid;
   sp.S[0] = (TwE<T>*)h->res_S;
   sp.S[1] = (TwE<T>*)h->res_S + h->n[0];
   const int rc = launch_static_phase<T>(sp, h->stream);
@@ -688,7 +710,8 @@ wp_status res1d_split_potential(wp_handle* h) {
   if (st != WP_OK) return st;
   // batched instances run on other streams: the tables are complete on return
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
-  h->res_static_mask = stat;
+  // the grid potential lives in the static tables (bit 31: tables in use without static terms)
+  h->res_static_mask = stat | (h->vgrid ? 0x80000000u : 0u);
   h->res_plane_mask = plane;
   h->res_gen_mask = gen;
   return WP_OK;
@@ -1050,7 +1073,7 @@ void batch_free_compiled(wp_batch* b) {
 }
 
 bool batchable_2d(const wp_handle* h) {
-  if (h->ndim != 2) return false;
+  if (h->ndim != 2 || h->vgrid) return false;
   for (int d = 0; d < 2; d++) {
     const PassPlan& pl = h->plan[d];
     if (pl.nthreads != 256 || pl.ept != 8 || ((int64_t)1 << (pl.logn + pl.logC)) != 2048) return false;
@@ -1287,6 +1310,22 @@ wp_status batch_step(wp_batch* b, int64_t m, bool use_graph) {
 }  // namespace
 
 // =================================================================== C ABI
+namespace wp {
+
+wp_status handle_set_error(wp_handle* h, wp_status st, const char* msg) { return fail(h, st, msg); }
+
+void handle_geometry(const wp_handle* h, int* ndim, int64_t n[3], double xmin[3], double dx[3], void** stream) {
+  *ndim = h->ndim;
+  for (int d = 0; d < 3; d++) {
+    n[d] = h->n[d];
+    xmin[d] = h->g.xmin[d];
+    dx[d] = h->g.dx[d];
+  }
+  *stream = (void*)h->stream;
+}
+
+}  // namespace wp
+
 extern "C" {
 
 const char* wp_status_string(wp_status s) {
@@ -1402,7 +1441,7 @@ wp_status wp_destroy(wp_handle* h) {
   cudaStreamSynchronize(h->stream);
   void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
                   h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
-                  h->lines_kin[1], h->res_S, h->gauss_tab};
+                  h->lines_kin[1], h->res_S, h->gauss_tab, h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& ep : h->pending) {
@@ -1439,6 +1478,31 @@ wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
   WP_CUDA(h, cudaMemcpy(h->dpot, &dp, sizeof(dp), cudaMemcpyHostToDevice));
   h->hpot = dp;
   if (h->ndim == 1) return res1d_split_potential(h);
+  return WP_OK;
+}
+
+wp_status wp_set_potential_grid(wp_handle* h, const double* V, int on_device) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (!V) {
+    for (void* q : {(void*)h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]})
+      if (q) cudaFree(q);
+    h->vgrid = nullptr;
+    h->vgrid_rec[0] = h->vgrid_rec[1] = nullptr;
+  } else {
+    const size_t bytes = (size_t)h->N * sizeof(double);
+    if (!h->vgrid) WP_CUDA(h, cudaMalloc(&h->vgrid, bytes));
+    WP_CUDA(h, cudaMemcpyAsync(h->vgrid, V, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               h->stream));
+    if (h->ndim > 1) {
+      for (int k = 0; k < 2; k++)
+        if (!h->vgrid_rec[k]) WP_CUDA(h, cudaMalloc(&h->vgrid_rec[k], (size_t)h->N * sizeof(TwE<double>)));
+      const wp_status st = WP_DISPATCH(h, grid_phase_tables<T>(h));
+      if (st != WP_OK) return st;
+    }
+  }
+  if (h->ndim == 1) return res1d_split_potential(h);
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
   return WP_OK;
 }
 

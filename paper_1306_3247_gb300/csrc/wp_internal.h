@@ -192,6 +192,8 @@ struct PassParams {
   const cx<T>* Ox;     // pass-axis observable tables (fixed-size kernels)
   const cx<T>* Ok;
   const T* AT;
+  const TwE<T>* grid_rec;  // static grid potential: phase records of this pass's tau, or NULL
+  const double* grid_v;    // static grid potential (observables), or NULL
 };
 
 // Per-line records of one pass (k_lines).
@@ -251,6 +253,7 @@ struct Res1dParams {
   uint32_t static_mask;
   uint32_t plane_mask;
   uint32_t gen_mask;
+  const double* vgrid;       // static grid potential (observables; the phase is in S), or NULL
   int32_t fixed;             // compile-time line length (k_res1d_fixed), n = 2^8 .. 2^14
   int32_t max_radix_log;     // largest butterfly of the run-time-length kernel (2 or 3)
   const void* Wst;           // per-stage twiddle records (fixed)
@@ -264,7 +267,17 @@ struct StaticPhaseParams {
   int64_t n;
   const DevPot* pot;
   uint32_t static_mask;
+  const double* vgrid; // static grid potential added to V_s, or NULL
   TwE<T>* S[2];        // exp(-i V_s dt / hbar), exp(-i V_s (dt/2) / hbar)
+};
+
+// Phase records of a static grid potential for dt and dt/2 (k_grid_phase).
+template <class T>
+struct GridPhaseParams {
+  const double* V;
+  int64_t n;
+  double dt, hbar;
+  TwE<T>* rec[2];
 };
 
 struct ReduceParams {
@@ -318,6 +331,7 @@ template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int nins
                                           int64_t nsteps, size_t smem, void* stream);
 int launch_reduce(const ReduceParams& p, void* stream);
 template <class T> int launch_static_phase(const StaticPhaseParams<T>& p, void* stream);
+template <class T> int launch_grid_phase(const GridPhaseParams<T>& p, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);
@@ -340,6 +354,10 @@ template <class T> int launch_res1d_fixed(const Res1dParams<T>& p, size_t smem, 
 template <class T> int launch_res1d_fixed_batch(const Res1dParams<T>* params, int ninst, int logn, int64_t nsteps,
                                                 size_t smem, void* stream);
 template <class T> int res1d_fixed_smem_limit_set(size_t smem);
+
+// Handle access for the run-time compiled potentials (wp_jit.cu).
+wp_status handle_set_error(wp_handle* h, wp_status st, const char* msg);
+void handle_geometry(const wp_handle* h, int* ndim, int64_t n[3], double xmin[3], double dx[3], void** stream);
 
 // Kernel classes for timing and launch counting.
 enum KernelClass : int {

@@ -816,16 +816,13 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
       if (ph) rec = sRec[l];
       const T* G0 = p.G[0][p.axis];
       const T* G1 = p.G[1][p.axis];
-      [[maybe_unused]] const cx<T>* z0 = nullptr;
-      [[maybe_unused]] int64_t zstep = 0;
-      if constexpr (OBS) {
-        if (f & F_AUTOCORR) {
-          int ll, ii;
-          int64_t base, es;
-          fixed_walk<T, SH>(p, o0, cb, ll, ii, base, es);
-          z0 = p.psi0 + base;
-          zstep = es * ISTEP;
-        }
+      // global index of point k of this thread: gbase + k gstep (autocorrelation, grid potential)
+      int64_t gbase = 0, gstep = 0;
+      if ((OBS && (f & F_AUTOCORR)) || p.grid_rec || (OBS && p.grid_v)) {
+        int ll, ii;
+        int64_t es;
+        fixed_walk<T, SH>(p, o0, cb, ll, ii, gbase, es);
+        gstep = es * ISTEP;
       }
 #pragma unroll
       for (int k = 0; k < 8; k++) {
@@ -835,6 +832,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           v = apply_factor_rec(v, p.Prec[i], rec.L);
           if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
           if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
+          if (p.grid_rec) v = tw_apply<false>(v, p.grid_rec[gbase + k * gstep]);
           s[i * LS + l] = v;
         }
         if constexpr (OBS) {
@@ -845,10 +843,11 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
             q[1] = madd(xx.re, rho, q[1]);
             q[2] = madd(xx.im, rho, q[2]);
             q[3] = madd(p.AT[i], rho, q[3]);
+            if (p.grid_v) q[3] = madd(T(p.grid_v[gbase + k * gstep]), rho, q[3]);
             if (p.ngauss > 0) q[4] = madd(G0[i], rho, q[4]);
             if (p.ngauss > 1) q[5] = madd(G1[i], rho, q[5]);
             if (f & F_AUTOCORR) {
-              const cx<T> c = cmulc(v, z0[k * zstep]);
+              const cx<T> c = cmulc(v, p.psi0[gbase + k * gstep]);
               q[6] = q[6] + c.re;
               q[7] = q[7] + c.im;
             }
@@ -862,6 +861,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
       if (f & F_PHASE) {
         v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
         for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
+        if (p.grid_rec) v = tw_apply<false>(v, p.grid_rec[tile_gidx(p, sh, o0, cb, i, l)]);
         s[i * LS + l] = v;
       }
       if (OBS && (f & F_OBS_POS)) {
@@ -885,6 +885,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           for (int d = 0; d < p.g.ndim; d++) prod *= p.Gd[gg][d][gi[d]];
           V += prod;
         }
+        if (p.grid_v) V += p.grid_v[tile_gidx(p, sh, o0, cb, i, l)];
         acc[Q_V] += V * rho;
         if (f & F_AUTOCORR) {
           const cx<T> z = p.psi0[tile_gidx(p, sh, o0, cb, i, l)];
@@ -1412,6 +1413,7 @@ __device__ void res1d_body(const Res1dParams<T>& p, const RS& rs, cx<T>* s) {
         const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, t) : term_axis_part(tm, 0, x, t);
         V += fco[k] * sh;
       }
+      if (p.vgrid) V += p.vgrid[i];
       acc[Q_RHO] += rho;
       acc[Q_X] += x * rho;
       acc[Q_XX] += x * x * rho;
@@ -1475,11 +1477,26 @@ __global__ void __launch_bounds__(256) k_static_phase(const StaticPhaseParams<T>
       const double sh = (tm.shape == WP_SHAPE_GAUSS) ? gauss_axis_factor(tm, 0, x, 0.0) : term_axis_part(tm, 0, x, 0.0);
       V += term_coef(tm, 0.0) * sh;
     }
+    if (p.vgrid) V += p.vgrid[i];
     double sn, cs;
     sincos(-V * p.g.dt / p.g.hbar, &sn, &cs);
     p.S[0][i] = make_rec<T>(cs, sn);
     sincos(-V * (0.5 * p.g.dt) / p.g.hbar, &sn, &cs);
     p.S[1][i] = make_rec<T>(cs, sn);
+  }
+}
+
+// Phase records exp(-i V_j tau / hbar) of a static grid potential for tau = dt and dt/2
+// (FP64 sincos, stored as records of T).
+template <class T>
+__global__ void __launch_bounds__(256) k_grid_phase(const GridPhaseParams<T> p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double V = p.V[i];
+    double sn, cs;
+    sincos(-V * p.dt / p.hbar, &sn, &cs);
+    p.rec[0][i] = make_rec<T>(cs, sn);
+    sincos(-V * (0.5 * p.dt) / p.hbar, &sn, &cs);
+    p.rec[1][i] = make_rec<T>(cs, sn);
   }
 }
 

@@ -101,6 +101,14 @@ int launch_static_phase(const StaticPhaseParams<T>& p, void* stream) {
 }
 
 template <class T>
+int launch_grid_phase(const GridPhaseParams<T>& p, void* stream) {
+  int64_t blocks = (p.n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks > 0) k_grid_phase<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
 int launch_convert(const ConvParams<T>& p, void* stream) {
   const int64_t blocks = (p.n + 255) / 256;
   if (blocks > 0) k_convert<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
@@ -183,6 +191,7 @@ int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, in
   template int launch_res1d<T>(const Res1dParams<T>&, size_t, void*);            \
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
   template int launch_static_phase<T>(const StaticPhaseParams<T>&, void*);        \
+  template int launch_grid_phase<T>(const GridPhaseParams<T>&, void*);            \
   template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
   template int launch_lines<T>(const LinesParams<T>&, void*);                    \
   template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, const int*, int, int64_t, int64_t, uint32_t, \

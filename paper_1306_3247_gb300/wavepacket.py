@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = True):
         "wp_kernel_count": ([], ctypes.c_int),
         "wp_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
         "wp_launch_count": ([H], ctypes.c_int64),
+        "wp_set_potential_grid": ([H, vp, ctypes.c_int], ctypes.c_int),
+        "wp_set_potential_source": ([H, ctypes.c_char_p], ctypes.c_int),
         "wp_get_schedule": ([H, P(WpSchedule)], ctypes.c_int),
         "wp_set_schedule": ([H, P(WpSchedule)], ctypes.c_int),
         "wp_autotune": ([H, ctypes.c_int32, P(WpSchedule), P(ctypes.c_double), P(ctypes.c_int32)], ctypes.c_int),
@@ -205,6 +207,16 @@ def wp_create(problem: WpProblem, stream=None):
 def wp_set_potential(h, pot: WpPotential):
     lib = load_library()
     _check(lib, h, lib.wp_set_potential(h, ctypes.byref(pot)))
+
+
+def wp_set_potential_grid(h, ptr, on_device: bool):
+    lib = load_library()
+    _check(lib, h, lib.wp_set_potential_grid(h, ctypes.c_void_p(ptr or 0), 1 if on_device else 0))
+
+
+def wp_set_potential_source(h, src: str):
+    lib = load_library()
+    _check(lib, h, lib.wp_set_potential_source(h, src.encode()))
 
 
 def wp_set_state(h, ptr: int, on_device: bool):
@@ -374,6 +386,28 @@ class Propagator:
 
     def set_potential(self, terms):
         wp_set_potential(self.h, make_potential(list(terms)))
+
+    def set_potential_grid(self, V):
+        """Static potential on the grid: numpy float64 (host) or torch float64 CUDA tensor
+        of the state's shape; None removes it."""
+        if V is None:
+            wp_set_potential_grid(self.h, None, False)
+        elif hasattr(V, "is_cuda") and V.is_cuda:
+            import torch
+            t = V.contiguous().to(torch.float64)
+            if tuple(t.shape) != self.shape:
+                raise ValueError(f"grid shape {tuple(t.shape)} != {self.shape}")
+            wp_set_potential_grid(self.h, t.data_ptr(), True)
+        else:
+            a = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+            if a.shape != self.shape:
+                raise ValueError(f"grid shape {a.shape} != {self.shape}")
+            wp_set_potential_grid(self.h, a.ctypes.data, False)
+
+    def set_potential_source(self, src: str):
+        """CUDA C source defining __device__ double wp_user_potential(double x, double y,
+        double z), compiled at run time and evaluated once on the grid."""
+        wp_set_potential_source(self.h, src)
 
     @property
     def schedule(self) -> dict:
