@@ -163,6 +163,22 @@ wp_status wp_step(wp_handle* h, int64_t nsteps);
 /* Evaluate the observables of Tab. 3 at the current step (synchronises). */
 wp_status wp_observe(wp_handle* h, wp_obs* out);
 
+/* User observables (Sec. 3.2.5: user_observe is called every nprint steps with the time
+ * and the wave function).
+ * wp_expect_grid: <psi|A|psi> = sum_j A_j |psi_j|^2 dV for a position-space operator given
+ * on the grid (FP64, n[0]*n[1]*n[2] values in the state's layout; host pointer when
+ * on_device = 0, device pointer when 1), at the current step; FP64 reduction in a fixed
+ * order (bitwise reproducible). Allocates a small temporary; synchronises.
+ * wp_run_callback: Algorithm 1 with a host function called on every record (the
+ * record of the current step first, then one after every nprint steps) with the handle,
+ * whose state is the state of the record (read it with wp_get_state, wp_state_ptr or
+ * wp_expect_grid; do not step it inside fn); fn returns 0 to continue, nonzero to stop
+ * after that record. *nrec receives the records delivered. The records equal wp_run's
+ * to rounding. */
+wp_status wp_expect_grid(wp_handle* h, const double* A, int on_device, double* out);
+typedef int (*wp_record_fn)(wp_handle* h, const wp_obs* rec, void* user);
+wp_status wp_run_callback(wp_handle* h, int64_t nt, int64_t nprint, wp_record_fn fn, void* user, int64_t* nrec);
+
 /* Algorithm 1: observables at the current step and after every nprint steps,
  * nt steps in all (all nt run even when nprint does not divide nt, Sec. 3.4).
  * obs: caller-owned host array of at least 1 + nt/nprint records; *nobs gets the count.

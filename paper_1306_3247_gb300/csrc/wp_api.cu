@@ -1506,6 +1506,69 @@ wp_status wp_set_potential_grid(wp_handle* h, const double* V, int on_device) {
   return WP_OK;
 }
 
+wp_status wp_expect_grid(wp_handle* h, const double* A, int on_device, double* out) {
+  if (!h || !A || !out) return fail(h, WP_EINVAL, "NULL argument");
+  const int64_t per_block = 8192;
+  const int64_t nb = (h->N + per_block - 1) / per_block;
+  const size_t abytes = on_device ? 0 : (size_t)h->N * sizeof(double);
+  char* tmp = nullptr;
+  WP_CUDA(h, cudaMalloc(&tmp, abytes + (size_t)(nb + 1) * sizeof(double)));
+  const double* Ad = A;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = cudaMemcpyAsync(tmp, A, abytes, cudaMemcpyHostToDevice, h->stream);
+    Ad = (const double*)tmp;
+  }
+  double* partial = (double*)(tmp + abytes);
+  wp_status st = WP_OK;
+  if (e != cudaSuccess) {
+    st = cuda_fail(h, e, "grid copy");
+  } else {
+    st = WP_DISPATCH(h, [&]() -> wp_status {
+      ExpectParams<T> p{};
+      p.psi = (const cx<T>*)h->state;
+      p.A = Ad;
+      p.n = h->N;
+      p.per_block = per_block;
+      p.partial = partial;
+      return launch_rc(h, launch_expect<T>(p, (int)nb, h->g.dv, partial + nb, h->stream), "expectation kernel");
+    }());
+  }
+  if (st == WP_OK) {
+    e = cudaMemcpyAsync(out, partial + nb, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = cuda_fail(h, e, "expectation result");
+  }
+  cudaStreamSynchronize(h->stream);
+  cudaFree(tmp);
+  return st;
+}
+
+wp_status wp_run_callback(wp_handle* h, int64_t nt, int64_t nprint, wp_record_fn fn, void* user, int64_t* nrec) {
+  if (!h || !fn) return fail(h, WP_EINVAL, "NULL argument");
+  if (nt < 1 || nprint <= 0 || nprint > nt) return fail(h, WP_EINVAL, "need 0 < nprint <= nt");
+  int64_t count = 0;
+  if (nrec) *nrec = 0;
+  wp_obs rec;
+  wp_status st = wp_observe(h, &rec);
+  if (st != WP_OK) return st;
+  count++;
+  if (nrec) *nrec = count;
+  if (fn(h, &rec, user)) return WP_OK;
+  for (int64_t done = 0; done < nt;) {
+    const int64_t m = std::min<int64_t>(nprint, nt - done);
+    if ((st = wp_step(h, m)) != WP_OK) return st;
+    done += m;
+    if (m < nprint) break;  // the tail after the last multiple of nprint has no record
+    if ((st = wp_observe(h, &rec)) != WP_OK) return st;
+    count++;
+    if (nrec) *nrec = count;
+    if (fn(h, &rec, user)) return WP_OK;
+  }
+  WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  return check_device_error(h);
+}
+
 wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
   if (!h || !psi) return fail(h, WP_EINVAL, "NULL argument");
   const size_t bytes128 = (size_t)h->N * 16;

@@ -271,6 +271,16 @@ struct StaticPhaseParams {
   TwE<T>* S[2];        // exp(-i V_s dt / hbar), exp(-i V_s (dt/2) / hbar)
 };
 
+// <psi|A|psi> partial sums per block (k_expect_partial) and their fixed-order total.
+template <class T>
+struct ExpectParams {
+  const cx<T>* psi;
+  const double* A;
+  int64_t n;
+  int64_t per_block;   // points per block
+  double* partial;     // [gridDim.x]
+};
+
 // Phase records of a static grid potential for dt and dt/2 (k_grid_phase).
 template <class T>
 struct GridPhaseParams {
@@ -332,6 +342,7 @@ template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int nins
 int launch_reduce(const ReduceParams& p, void* stream);
 template <class T> int launch_static_phase(const StaticPhaseParams<T>& p, void* stream);
 template <class T> int launch_grid_phase(const GridPhaseParams<T>& p, void* stream);
+template <class T> int launch_expect(const ExpectParams<T>& p, int nblocks, double dv, double* out, void* stream);
 int launch_set_step(Ctrl* ctrl, int64_t step, void* stream);
 int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);

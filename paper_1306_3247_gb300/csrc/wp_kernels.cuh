@@ -1500,6 +1500,38 @@ __global__ void __launch_bounds__(256) k_grid_phase(const GridPhaseParams<T> p) 
   }
 }
 
+// User expectation value <psi|A|psi> (Sec. 3.2.5): per-block FP64 sums over a fixed
+// range of points, then one block sums the partials in order.
+template <class T>
+__global__ void __launch_bounds__(256) k_expect_partial(const ExpectParams<T> p) {
+  __shared__ double red[32][NQ];
+  __shared__ double tot[NQ];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  const int64_t b0 = (int64_t)blockIdx.x * p.per_block;
+  const int64_t b1 = b0 + p.per_block < p.n ? b0 + p.per_block : p.n;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const cx<T> v = p.psi[i];
+    const double re = (double)v.re, im = (double)v.im;
+    acc[0] += p.A[i] * (re * re + im * im);
+  }
+  block_sum(acc, tot, red);
+  if (threadIdx.x == 0) p.partial[blockIdx.x] = tot[0];
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_expect_final(const double* partial, int nblocks, double dv, double* out) {
+  __shared__ double red[32][NQ];
+  __shared__ double tot[NQ];
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc[0] += partial[b];
+  block_sum(acc, tot, red);
+  if (threadIdx.x == 0) *out = tot[0] * dv;
+}
+
 // Batched resident lines: block b runs instance b (all of one line length) for nsteps.
 template <class T, class RS>
 __device__ __forceinline__ void res1d_batch_body(const Res1dParams<T>* __restrict__ params, int64_t nsteps,

@@ -109,6 +109,14 @@ int launch_grid_phase(const GridPhaseParams<T>& p, void* stream) {
 }
 
 template <class T>
+int launch_expect(const ExpectParams<T>& p, int nblocks, double dv, double* out, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  k_expect_partial<T><<<(unsigned)nblocks, 256, 0, st>>>(p);
+  k_expect_final<T><<<1, 256, 0, st>>>(p.partial, nblocks, dv, out);
+  return cuda_status(cudaGetLastError());
+}
+
+template <class T>
 int launch_convert(const ConvParams<T>& p, void* stream) {
   const int64_t blocks = (p.n + 255) / 256;
   if (blocks > 0) k_convert<T><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(p);
@@ -192,6 +200,7 @@ int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, in
   template int launch_convert<T>(const ConvParams<T>&, void*);                    \
   template int launch_static_phase<T>(const StaticPhaseParams<T>&, void*);        \
   template int launch_grid_phase<T>(const GridPhaseParams<T>&, void*);            \
+  template int launch_expect<T>(const ExpectParams<T>&, int, double, double*, void*); \
   template int launch_gaussian<T>(const GaussParams<T>&, int64_t, void*);        \
   template int launch_lines<T>(const LinesParams<T>&, void*);                    \
   template int launch_pass_batch<T>(const PassParams<T>*, const int64_t*, const int*, int, int64_t, int64_t, uint32_t, \

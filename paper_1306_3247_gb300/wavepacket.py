@@ -62,6 +62,9 @@ class WpSchedule(ctypes.Structure):
                 ("fixed", ctypes.c_int32)]
 
 
+RECORD_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class WavepacketError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{message} (status {status})")
@@ -108,6 +111,8 @@ def load_library(build_if_missing: bool = True):
         "wp_kernel_name": ([ctypes.c_int], ctypes.c_char_p),
         "wp_launch_count": ([H], ctypes.c_int64),
         "wp_set_potential_grid": ([H, vp, ctypes.c_int], ctypes.c_int),
+        "wp_expect_grid": ([H, vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
+        "wp_run_callback": ([H, ctypes.c_int64, ctypes.c_int64, RECORD_FN, vp, P(ctypes.c_int64)], ctypes.c_int),
         "wp_set_potential_source": ([H, ctypes.c_char_p], ctypes.c_int),
         "wp_get_schedule": ([H, P(WpSchedule)], ctypes.c_int),
         "wp_set_schedule": ([H, P(WpSchedule)], ctypes.c_int),
@@ -212,6 +217,35 @@ def wp_set_potential(h, pot: WpPotential):
 def wp_set_potential_grid(h, ptr, on_device: bool):
     lib = load_library()
     _check(lib, h, lib.wp_set_potential_grid(h, ctypes.c_void_p(ptr or 0), 1 if on_device else 0))
+
+
+def wp_expect_grid(h, ptr: int, on_device: bool) -> float:
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    _check(lib, h, lib.wp_expect_grid(h, ctypes.c_void_p(ptr), 1 if on_device else 0, ctypes.byref(out)))
+    return out.value
+
+
+def wp_run_callback(h, nt: int, nprint: int, fn):
+    """fn(handle, record) -> truthy to stop; returns the number of records delivered."""
+    lib = load_library()
+    err = []
+
+    def tramp(hp, rec_ptr, user):
+        try:
+            rec = _obs_array(rec_ptr, 1)[0]
+            return 1 if fn(hp, rec) else 0
+        except Exception as e:  # stop the run and re-raise after it returns
+            err.append(e)
+            return 1
+
+    cb = RECORD_FN(tramp)
+    n = ctypes.c_int64(0)
+    st = lib.wp_run_callback(h, int(nt), int(nprint), cb, None, ctypes.byref(n))
+    if err:
+        raise err[0]
+    _check(lib, h, st)
+    return n.value
 
 
 def wp_set_potential_source(h, src: str):
@@ -403,6 +437,22 @@ class Propagator:
             if a.shape != self.shape:
                 raise ValueError(f"grid shape {a.shape} != {self.shape}")
             wp_set_potential_grid(self.h, a.ctypes.data, False)
+
+    def expect_grid(self, A) -> float:
+        """<psi|A|psi> for a position-space operator on the grid (numpy or CUDA tensor)."""
+        if hasattr(A, "is_cuda") and A.is_cuda:
+            import torch
+            t = A.contiguous().to(torch.float64)
+            return wp_expect_grid(self.h, t.data_ptr(), True)
+        a = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+        if a.shape != self.shape:
+            raise ValueError(f"operator shape {a.shape} != {self.shape}")
+        return wp_expect_grid(self.h, a.ctypes.data, False)
+
+    def run_with_callback(self, nt: int, nprint: int, fn):
+        """Algorithm 1 with fn(propagator, record) called on every record (the state is
+        the record's); a truthy return stops the run. Returns the records delivered."""
+        return wp_run_callback(self.h, nt, nprint, lambda hp, rec: fn(self, rec))
 
     def set_potential_source(self, src: str):
         """CUDA C source defining __device__ double wp_user_potential(double x, double y,
