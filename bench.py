@@ -197,9 +197,9 @@ def pass_flops_per_point(logn, kind):
     return {"pass_contig": 2 * fft + 6, "pass_kinetic": 2 * fft + 6, "pass_strided": fft}.get(kind, fft)
 
 
-def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False):
+def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False, order="vkv"):
     import torch
-    cfg = W.config_3d_barrier(n=args.grid)
+    cfg = W.config_3d_barrier(n=args.grid, order=order)
     pb, terms = cfg["problem"], cfg["terms"]
     nprint = cfg["nprint"]
     npts = math.prod(pb["n"][: pb["ndim"]])
@@ -400,6 +400,10 @@ def main():
             r["roofline"]["frac"] = r["roofline"]["achieved"] / pk["hbm_gbs"]
             r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
             extra.setdefault("forms", {})[form] = r
+        # the paper's K-V-K order (eq. splitop, Algorithm 1) on the same job, native FP64
+        r = bench_3d(args, WPK, "c128", 1, local, args.steps, 1, args.nt, with_e2e=False, order="kvk")
+        extra["orders"] = {"kvk": {"value": r["value"], "ms_per_job": r["ms_per_job"], "precision": "c128",
+                                   "kernels": r["kernels"]}}
         extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=3, warmup=3,
                                          plain_subset=64, autotune=args.autotune)
         extra["served"] = bench_served(WPK, args.serve_requests, "c64")

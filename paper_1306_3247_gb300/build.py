@@ -15,6 +15,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libwavepacket_gpu.so")
 SOURCES = ["wp_api.cu", "wp_kernels_f64.cu", "wp_kernels_f32.cu", "wp_kernels_ff.cu", "wp_fixed_f64.cu",
            "wp_fixed_f32.cu", "wp_fixed_ff.cu", "wp_fixed_obs_f64.cu", "wp_fixed_obs_f32.cu", "wp_fixed_obs_ff.cu",
+           "wp_fixed_grid_f64.cu", "wp_fixed_grid_f32.cu", "wp_fixed_grid_ff.cu",
            "wp_batch_f64_contig.cu", "wp_batch_f64_strided.cu", "wp_batch_f32_contig.cu", "wp_batch_f32_strided.cu",
            "wp_batch_ff_contig.cu", "wp_batch_ff_strided.cu", "wp_res1d_f64.cu", "wp_res1d_f32.cu", "wp_res1d_ff.cu",
            "wp_noalloc.cu", "wp_server.cu", "wp_jit.cu"]

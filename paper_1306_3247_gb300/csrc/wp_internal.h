@@ -359,6 +359,10 @@ template <class T> int launch_pass_batch_strided(const PassParams<T>* params, co
                                                  uint32_t flags, int khalf, size_t smem, void* stream);
 template <class T> int launch_fixed_obs(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 template <class T> int fixed_obs_smem_limit_set(size_t smem);
+template <class T> int launch_fixed_grid(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
+template <class T> int fixed_grid_smem_limit_set(size_t smem);
+template <class T> int launch_fixed_grid_obs(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
+template <class T> int fixed_grid_obs_smem_limit_set(size_t smem);
 template <class T> int res1d_smem_limit_set(size_t smem);
 // fixed-length resident-line kernels (their own translation units, wp_res1d_*.cu)
 template <class T> int launch_res1d_fixed(const Res1dParams<T>& p, size_t smem, void* stream);

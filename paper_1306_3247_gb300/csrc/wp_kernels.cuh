@@ -769,7 +769,7 @@ __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[
 
 // Everything a pass does once its tile is in shared memory: the transforms and factors
 // selected by the flags, the store, the partial sums. Ends with a block barrier.
-template <class T, int E, bool OBS, class SH>
+template <class T, int E, bool OBS, class SH, bool GRID = false>
 __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& sh, cx<T>* s, int64_t tile) {
   __shared__ double red[32][NQ];
   __shared__ double tot[NQ];
@@ -816,13 +816,15 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
       if (ph) rec = sRec[l];
       const T* G0 = p.G[0][p.axis];
       const T* G1 = p.G[1][p.axis];
-      // global index of point k of this thread: gbase + k gstep (autocorrelation, grid potential)
-      int64_t gbase = 0, gstep = 0;
-      if ((OBS && (f & F_AUTOCORR)) || p.grid_rec || (OBS && p.grid_v)) {
-        int ll, ii;
-        int64_t es;
-        fixed_walk<T, SH>(p, o0, cb, ll, ii, gbase, es);
-        gstep = es * ISTEP;
+      // global index of point k of this thread: gbase + k gstep (autocorrelation)
+      [[maybe_unused]] int64_t gbase = 0, gstep = 0;
+      if constexpr (OBS && !GRID) {
+        if (f & F_AUTOCORR) {
+          int ll, ii;
+          int64_t es;
+          fixed_walk<T, SH>(p, o0, cb, ll, ii, gbase, es);
+          gstep = es * ISTEP;
+        }
       }
 #pragma unroll
       for (int k = 0; k < 8; k++) {
@@ -832,7 +834,6 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           v = apply_factor_rec(v, p.Prec[i], rec.L);
           if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
           if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
-          if (p.grid_rec) v = tw_apply<false>(v, p.grid_rec[gbase + k * gstep]);
           s[i * LS + l] = v;
         }
         if constexpr (OBS) {
@@ -843,13 +844,40 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
             q[1] = madd(xx.re, rho, q[1]);
             q[2] = madd(xx.im, rho, q[2]);
             q[3] = madd(p.AT[i], rho, q[3]);
-            if (p.grid_v) q[3] = madd(T(p.grid_v[gbase + k * gstep]), rho, q[3]);
             if (p.ngauss > 0) q[4] = madd(G0[i], rho, q[4]);
             if (p.ngauss > 1) q[5] = madd(G1[i], rho, q[5]);
-            if (f & F_AUTOCORR) {
+            if (!GRID && (f & F_AUTOCORR)) {  // GRID: after the grid phase, below
               const cx<T> c = cmulc(v, p.psi0[gbase + k * gstep]);
               q[6] = q[6] + c.re;
               q[7] = q[7] + c.im;
+            }
+          }
+        }
+      }
+      // static grid potential (GRID variant only): its phase records and its
+      // potential-energy sum
+      if constexpr (GRID) {
+        int ll, ii;
+        int64_t gb, es;
+        fixed_walk<T, SH>(p, o0, cb, ll, ii, gb, es);
+        const int64_t gs = es * ISTEP;
+        const bool gph = ph && p.grid_rec != nullptr;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+          const int i = i0 + k * ISTEP;
+          cx<T> v = s[i * LS + l];
+          if (gph) {
+            v = tw_apply<false>(v, p.grid_rec[gb + k * gs]);
+            s[i * LS + l] = v;
+          }
+          if constexpr (OBS) {
+            if (f & F_OBS_POS) {
+              if (p.grid_v) q[3] = madd(T(p.grid_v[gb + k * gs]), norm2(v), q[3]);
+              if (f & F_AUTOCORR) {
+                const cx<T> c = cmulc(v, p.psi0[gb + k * gs]);
+                q[6] = q[6] + c.re;
+                q[7] = q[7] + c.im;
+              }
             }
           }
         }
@@ -989,7 +1017,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
 }
 
 // One tile per block: synchronous load, then compute.
-template <class T, int E, bool OBS, class SH>
+template <class T, int E, bool OBS, class SH, bool GRID = false>
 __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, cx<T>* s) {
   const int64_t tile = blockIdx.x;
   if constexpr (SH::fixed) {
@@ -1004,7 +1032,7 @@ __device__ __forceinline__ void pass_body(const PassParams<T>& p, const SH& sh, 
     }
   }
   __syncthreads();
-  pass_compute<T, E, OBS>(p, sh, s, tile);
+  pass_compute<T, E, OBS, SH, GRID>(p, sh, s, tile);
 }
 
 // E elements per thread; the block has at most 32 E threads, so a tile holds at most
@@ -1092,10 +1120,11 @@ __global__ void __launch_bounds__(256) k_lines_batch(const LinesParams<T>* __res
 }
 
 // Fixed-size pass: n = 2^LOGN points per line, 2048-element tiles, 256 threads.
-template <class T, int LOGN, bool CONTIG, bool OBS>
+// GRID: the variant that also applies a static grid potential (contiguous passes only).
+template <class T, int LOGN, bool CONTIG, bool OBS, bool GRID = false>
 __global__ void __launch_bounds__(256) k_pass_fixed(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  pass_body<T, 8, OBS>(p, FixShape<LOGN, CONTIG>(), reinterpret_cast<cx<T>*>(smem_raw));
+  pass_body<T, 8, OBS, FixShape<LOGN, CONTIG>, GRID>(p, FixShape<LOGN, CONTIG>(), reinterpret_cast<cx<T>*>(smem_raw));
 }
 
 // ------------------------------------------------------------------ per-line records

@@ -12,6 +12,8 @@ template <class T>
 int pass_smem_limit_set(size_t smem) {
   cudaError_t e = (cudaError_t)fixed_smem_limit_set<T>(smem);
   if (e == cudaSuccess) e = (cudaError_t)fixed_obs_smem_limit_set<T>(smem);
+  if (e == cudaSuccess) e = (cudaError_t)fixed_grid_smem_limit_set<T>(smem);
+  if (e == cudaSuccess) e = (cudaError_t)fixed_grid_obs_smem_limit_set<T>(smem);
   const int a = cudaFuncAttributeMaxDynamicSharedMemorySize;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, false>, (cudaFuncAttribute)a, (int)smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass<T, 8, true>, (cudaFuncAttribute)a, (int)smem);
@@ -42,11 +44,18 @@ int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* strea
   cudaStream_t st = (cudaStream_t)stream;
   if (p.fixed) {
     if (p.nthreads != 256 || p.logC != 11 - p.logn) return (int)cudaErrorInvalidConfiguration;
-    if (!obs) return launch_fixed<T>(p, grid.x, smem, stream);
-    // the fixed variant sums positions on the contiguous axis, momenta on a strided one
     const bool contig = p.log_inner == 0;
-    if ((contig && !(p.flags & F_OBS_MOM)) || (!contig && !(p.flags & F_OBS_POS)))
-      return launch_fixed_obs<T>(p, grid.x, smem, stream);
+    // a static grid potential enters the potential phase and the position sums
+    const bool use_grid = (p.grid_rec && (p.flags & F_PHASE)) || (p.grid_v && (p.flags & F_OBS_POS));
+    if (use_grid) {
+      if (contig && !(p.flags & F_OBS_MOM))
+        return obs ? launch_fixed_grid_obs<T>(p, grid.x, smem, stream) : launch_fixed_grid<T>(p, grid.x, smem, stream);
+    } else {
+      if (!obs) return launch_fixed<T>(p, grid.x, smem, stream);
+      // the fixed variant sums positions on the contiguous axis, momenta on a strided one
+      if ((contig && !(p.flags & F_OBS_MOM)) || (!contig && !(p.flags & F_OBS_POS)))
+        return launch_fixed_obs<T>(p, grid.x, smem, stream);
+    }
   }
   if (p.ept == 8 && p.nthreads <= 256) {
     if (obs)
