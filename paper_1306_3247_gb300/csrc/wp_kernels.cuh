@@ -1043,23 +1043,12 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
   pass_body<T, E, OBS>(p, DynShape(p), reinterpret_cast<cx<T>*>(smem_raw));
 }
 
-// Batched pass over many instances: tile_start[k] is the first block of instance k (a
-// prefix sum of the instances' tile counts) and block_inst[b] the instance of block b;
-// every instance tiles its lines into 2048-element tiles with 256 threads. The block
-// copies its instance's parameters to shared memory and runs the pass body: the
-// compile-time-shape body (with per-line records) for n = 64..1024, the run-time one
-// otherwise.
-template <class T, int LOGN, bool CONTIG>
-__device__ __forceinline__ void batch_fixed(const PassParams<T>& p, cx<T>* s, int64_t tile) {
-  const FixShape<LOGN, CONTIG> sh;
-  fixed_load<T, FixShape<LOGN, CONTIG>>(p, s, tile);
-  __syncthreads();
-  pass_compute<T, 8, false>(p, sh, s, tile);
-}
-
 // Batched pass over the instances of one shape class: block b of the launch is block
-// block_off + b of the class-sorted block list, serving tile (block - tile_start[inst]) of
-// instance block_inst[block]. LOGN = 6..10: fixed-size tiles; LOGN = 0: run-time shape.
+// block_off + b of the class-sorted block list (tile_start[k]: first block of instance k),
+// serving tile (block - tile_start[inst]) of instance block_inst[block]. Every instance
+// tiles its lines into 2048-element tiles with 256 threads. The block copies its
+// instance's parameters to shared memory and runs the pass body: LOGN = 6..10 the
+// compile-time-shape body (with per-line records), LOGN = 0 the run-time one.
 template <class T, bool CONTIG, int LOGN>
 __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
                                                     const int64_t* __restrict__ tile_start,
@@ -1070,6 +1059,32 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
   PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
   const int64_t blk = block_off + blockIdx.x;
   const int inst = block_inst[blk];
+  const int64_t tile = blk - tile_start[inst];
+  // fixed shapes: the tile loads need only the state pointer and the axis stride, so they
+  // are issued before the parameter copy and the two latencies overlap
+  [[maybe_unused]] cx<T> v[8];
+  [[maybe_unused]] int vl = 0, vi0 = 0;
+  if constexpr (LOGN > 0) {
+    using SH = FixShape<LOGN, CONTIG>;
+    constexpr int ISTEP = 256 >> SH::logC;
+    const cx<T>* in = params[inst].in;
+    const int li = params[inst].log_inner;
+    vl = threadIdx.x & ((1 << SH::logC) - 1);
+    vi0 = threadIdx.x >> SH::logC;
+    int64_t base, es;
+    if (CONTIG) {
+      base = (((tile << SH::logC) + vl) << SH::logn) + vi0;
+      es = 1;
+    } else {
+      const int tpo = li - SH::logC;
+      const int64_t o0 = tile >> tpo, cb = (tile & ((int64_t(1) << tpo) - 1)) << SH::logC;
+      es = int64_t(1) << li;
+      base = (((o0 << SH::logn) + vi0) << li) + cb + vl;
+    }
+    const cx<T>* q = in + base;
+#pragma unroll
+    for (int k = 0; k < 8; k++) v[k] = q[k * es * ISTEP];
+  }
   const int* src = reinterpret_cast<const int*>(&params[inst]);
   for (int k = threadIdx.x; k < (int)(sizeof(PassParams<T>) / sizeof(int)); k += blockDim.x)
     reinterpret_cast<int*>(raw)[k] = src[k];
@@ -1086,10 +1101,14 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
     }
   }
   __syncthreads();
-  const int64_t tile = blk - tile_start[inst];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   if constexpr (LOGN > 0) {
-    batch_fixed<T, LOGN, CONTIG>(p, s, tile);
+    using SH = FixShape<LOGN, CONTIG>;
+    constexpr int ISTEP = 256 >> SH::logC;
+#pragma unroll
+    for (int k = 0; k < 8; k++) s[(vi0 + k * ISTEP) * SH::LS + vl] = v[k];
+    __syncthreads();
+    pass_compute<T, 8, false>(p, SH(), s, tile);
   } else {
     const DynShape sh(p);
     int64_t o0, cb;
