@@ -42,6 +42,7 @@ MUTANTS = {
                              "double x[3] = {coord(p, 0, i), p->ndim > 1 ? coord(p, 1, i) : 0.0,\n"
                              "                       p->ndim > 2 ? coord(p, 2, k) : 0.0};\n"
                              "        int64_t idx = (i * n1 + j) * n2 + k;\n        double v"),
+    "morse_sign": ("double e = 1.0 - exp(-tm->a[1] * u);", "double e = 1.0 - exp(tm->a[1] * u);"),
     "grid_dropped_in_phase": ("double v = orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0);",
                               "double v = orc_potential_at(p, nterms, terms, x, t);"),
     "grid_dropped_in_energy": ("sv += (orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0)) * rho;",
@@ -60,6 +61,7 @@ PIN_TESTS = [
     lambda: PINS.test_potential_terms_pointwise(),
     lambda: PINS.test_constant_grid_potential_is_a_global_phase("vkv"),
     lambda: PINS.test_harmonic_grid_potential_ground_state_3d(),
+    lambda: PINS.test_morse_eigenstates_energy_and_stationarity(),
 ]
 
 

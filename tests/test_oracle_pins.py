@@ -425,3 +425,24 @@ def test_grid_adds_to_the_terms():
     a = O.propagate(pb, full, psi0, 15)
     b = O.propagate(dict(pb, vgrid=V), half, psi0, 15)
     assert rel_l2(b, a) < 1e-13
+
+
+# --------------------------------------------------------------------------- Morse (Sec. 4.1)
+def test_morse_eigenstates_energy_and_stationarity():
+    # the CO Morse potential of Sec. 4.1 on its grid: the closed-form bound states
+    # (Morse 1929) have E_v = hbar w (v + 1/2) - (hbar w (v + 1/2))^2 / 4D, and the ground
+    # state only turns its phase, e^{-i E_0 t / hbar}
+    cfg = W.config_1d_co_morse()
+    pb, terms = cfg["problem"], cfg["terms"]
+    M = W.CO_MORSE
+    dx = pb["L"][0] / pb["n"][0]
+    states = [W.morse_eigenstate(pb, v, M["D"], M["a"], M["xe"], W.CO_MASS) for v in range(3)]
+    for psi, e in states:
+        rec = O.observe(pb, [terms[0]], psi)
+        assert abs(rec[1] - 1.0) < 1e-13
+        assert abs(rec[11] - e) < 1e-12 * e
+    phi0, e0 = states[0]
+    psi = O.propagate(pb, [terms[0]], phi0, 2000)
+    ov = np.vdot(phi0, psi) * dx
+    assert abs(abs(ov) - 1.0) < 1e-12
+    assert abs(ov - np.exp(-1j * e0 * 2000 * pb["dt"])) < 1e-6
