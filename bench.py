@@ -273,8 +273,10 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
 
 def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, autotune=True):
     """The uneven-instance batch: all instances advance `chunk` steps per bench step.
-    With autotune, one instance of every distinct shape is tuned first; the cached
-    schedules then apply to all instances of that shape."""
+    With autotune, one instance of every distinct 1-D shape is tuned first; the cached
+    schedules then apply to all instances of that shape. 2-D instances keep the default
+    schedule: the batched 2-D passes run the 2048-element-tile kernels, and an instance
+    tuned to another tiling would leave the batched launch for its own sequence."""
     import torch
     inst = W.batched_instances(count=count)
     pts = [math.prod(c["problem"]["n"][: c["problem"]["ndim"]]) for c in inst]
@@ -282,7 +284,7 @@ def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, aut
     if autotune:
         for c in inst:
             key = tuple(c["problem"]["n"][: c["problem"]["ndim"]])
-            if key in tuned:
+            if key in tuned or c["problem"]["ndim"] != 1:
                 continue
             with WPK.Propagator(c["problem"], c["terms"], precision) as T:
                 T.init_gaussian(**c["init"])
@@ -308,6 +310,8 @@ def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, aut
            "steps_per_bench_step": chunk, "ms_per_bench_step": el / steps * 1e3, "graph_launches_issued": launches,
            "n1d": sum(1 for c in inst if c["problem"]["ndim"] == 1), "finite": finite, "precision": precision,
            "autotuned_shapes": {"x".join(map(str, k)): v for k, v in tuned.items()}}
+    if plain_subset <= 0:
+        return out
     # plain per-instance FP64 form on a subset of the same instances, one handle at a time
     sub = inst[:plain_subset]
     handles = []
@@ -415,6 +419,12 @@ def main():
                                    "kernels": r["kernels"]}}
         extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=3, warmup=3,
                                          plain_subset=64, autotune=args.autotune)
+        # the same batch in the complex128-accuracy forms (native FP64 and float-float)
+        extra["batched_forms"] = {}
+        for form in ("c128", "c128f"):
+            r = bench_batched(WPK, form, args.batch_count, chunk=20, steps=3, warmup=1, plain_subset=0,
+                              autotune=args.autotune)
+            extra["batched_forms"][form] = {k: r[k] for k in ("value", "ms_per_bench_step", "precision")}
         extra["served"] = bench_served(WPK, args.serve_requests, "c64")
     cpu = None
     if rank == 0 and not args.no_cpu:

@@ -221,7 +221,8 @@ wp_status wp_set_step_index(wp_handle* h, int64_t s);
  *
  * wp_autotune times every candidate schedule on the handle (`steps` steps each after one
  * warm-up step, CUDA events on the handle's stream), on a device copy of the state that
- * is put back afterwards together with the step index, applies the fastest, and stores it
+ * is put back afterwards together with the step index, applies the fastest (the default
+ * unless another is more than 2 % faster), and stores it
  * in a process-wide cache keyed by (precision, ndim, extents, order). wp_create applies a
  * cached schedule to every later handle of the same key (batched and served instances
  * included). best_ms is the best time per step; ncandidates counts the schedules timed.
