@@ -196,7 +196,8 @@ def pass_flops_per_point(logn, kind):
     return {"pass_contig": 2 * fft + 6, "pass_kinetic": 2 * fft + 6, "pass_strided": fft}.get(kind, fft)
 
 
-def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False, order="vkv"):
+def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=True, with_clocks=False, order="vkv",
+             keep_state=False):
     import torch
     cfg = W.config_3d_barrier(n=args.grid, order=order)
     pb, terms = cfg["problem"], cfg["terms"]
@@ -249,7 +250,8 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     clk = clocks.stop() if clocks else None
     dev_ms = max_over_ranks(world, dev_ms)
     out = {"value": world * npts * nt * steps / (dev_ms / 1e3), "ms_per_job": dev_ms / steps, "launches": launches,
-           "clocks": clk, "final_norm": float(obs["norm"][-1]), "autotune": tuned}
+           "clocks": clk, "final_norm": float(obs["norm"][-1]),
+           "norm_drift": float(abs(obs["norm"][-1] - obs["norm"][0])), "autotune": tuned}
     if with_e2e:
         job_e2e()
         torch.cuda.synchronize()
@@ -267,6 +269,8 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     prof = P.profile_read()
     P.profile(False)
     out["kernels"] = {k: {"launches": v[0], "avg_ms": v[1] / v[0]} for k, v in prof.items() if v[0]}
+    if keep_state:  # the final state of the job just run, for the error of the other forms
+        out["state"] = P.get_state_device(torch.empty(P.shape, dtype=torch.complex128, device="cuda"))
     P.close()
     return out
 
@@ -377,7 +381,8 @@ def main():
 
     torch.cuda.set_device(local)
     head = bench_3d(args, WPK, args.precision, world, local, args.steps, args.warmup, args.nt, with_e2e=True,
-                    with_clocks=True)
+                    with_clocks=True, keep_state=(args.precision == "c128" and not args.no_extra and rank == 0))
+    ref_state = head.pop("state", None)
     pk, src = peaks()
     npts = args.grid ** 3
     logn = int(math.log2(args.grid))
@@ -404,7 +409,8 @@ def main():
         for form in ("c128f", "c64"):
             if form == args.precision:
                 continue
-            r = bench_3d(args, WPK, form, 1, local, args.steps, 1, args.nt, with_e2e=False)
+            r = bench_3d(args, WPK, form, 1, local, args.steps, 1, args.nt, with_e2e=False,
+                         keep_state=ref_state is not None)
             kd = max(r["kernels"].items(), key=lambda kv: kv[1]["launches"] * kv[1]["avg_ms"])
             el = 8 if form == "c64" else 16
             r["roofline"] = {"bound": "hbm", "kernel": kd[0],
@@ -412,6 +418,12 @@ def main():
                              "unit": "GB/s", "traffic": traffic_of(args.grid, form, kd[0])}
             r["roofline"]["frac"] = r["roofline"]["achieved"] / pk["hbm_gbs"]
             r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
+            st = r.pop("state", None)
+            if st is not None and ref_state is not None:
+                # error of the form against the native FP64 result of the same job (which
+                # the parity tests pin to the FP64 oracle)
+                r["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(st - ref_state) /
+                                            torch.linalg.vector_norm(ref_state))
             extra.setdefault("forms", {})[form] = r
         # the paper's K-V-K order (eq. splitop, Algorithm 1) on the same job, native FP64
         r = bench_3d(args, WPK, "c128", 1, local, args.steps, 1, args.nt, with_e2e=False, order="kvk")
