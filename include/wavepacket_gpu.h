@@ -160,6 +160,14 @@ wp_status wp_get_state(wp_handle* h, void* dst, int on_device);
  * Asynchronous on the handle's stream. */
 wp_status wp_step(wp_handle* h, int64_t nsteps);
 
+/* CUDA-graph replay of wp_step: the second call with a given nsteps captures that chunk's
+ * launches as a graph and every later call replays it (the launches read the step index
+ * and the potential from device memory, so a replay advances from the current step).
+ * On by default for a handle created with a stream, unavailable on the legacy default
+ * stream (WP_EINVAL). Setting the potential, a grid or a schedule, or profiling, drops
+ * the captured graphs. This part has no counterpart in the paper. */
+wp_status wp_set_graphs(wp_handle* h, int enable);
+
 /* Evaluate the observables of Tab. 3 at the current step (synchronises). */
 wp_status wp_observe(wp_handle* h, wp_obs* out);
 

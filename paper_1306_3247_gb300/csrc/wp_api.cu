@@ -93,6 +93,9 @@ struct wp_handle {
   int64_t host_step = 0;
   int64_t launches = 0;
   bool profiling = false;
+  bool graphs_on = false;                     // replay wp_step chunks as CUDA graphs
+  std::map<int64_t, cudaGraphExec_t> graphs;  // per chunk length
+  std::map<int64_t, int> graph_seen;
   std::vector<EventPair> pending;
   std::vector<cudaEvent_t> free_events;
   double prof_ms[K_NCLASSES] = {};
@@ -110,6 +113,14 @@ wp_status fail(wp_handle* h, wp_status st, const std::string& msg) {
   else
     g_err = msg;
   return st;
+}
+
+// Drops the handle's captured chunks: called whenever what a chunk launches changes
+// (potential, grid, schedule, profiling).
+void graphs_clear(wp_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  h->graph_seen.clear();
 }
 
 wp_status cuda_fail(wp_handle* h, cudaError_t e, const char* what) {
@@ -603,6 +614,7 @@ wp_status apply_schedule(wp_handle* h, const wp_schedule& sc) {
     h->plan[0] = make_plan(h, 0, sc);
   }
   h->sched = sc;
+  graphs_clear(h);
   return WP_OK;
 }
 
@@ -1365,6 +1377,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
   if (!h) return fail(nullptr, WP_ENOMEM, "host allocation failed");
   h->pb = *pb;
   h->stream = (cudaStream_t)stream;
+  h->graphs_on = stream != nullptr;
   h->ndim = pb->ndim;
   h->prec = pb->precision;
   h->elem = (h->prec == WP_C64) ? 8 : 16;
@@ -1439,6 +1452,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
 wp_status wp_destroy(wp_handle* h) {
   if (!h) return WP_OK;
   cudaStreamSynchronize(h->stream);
+  graphs_clear(h);
   void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
                   h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
                   h->lines_kin[1], h->res_S, h->gauss_tab, h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]};
@@ -1477,6 +1491,7 @@ wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
   WP_CUDA(h, cudaMemcpy(h->dpot, &dp, sizeof(dp), cudaMemcpyHostToDevice));
   h->hpot = dp;
+  graphs_clear(h);
   if (h->ndim == 1) return res1d_split_potential(h);
   return WP_OK;
 }
@@ -1484,6 +1499,7 @@ wp_status wp_set_potential(wp_handle* h, const wp_potential* pot) {
 wp_status wp_set_potential_grid(wp_handle* h, const double* V, int on_device) {
   if (!h) return fail(h, WP_EINVAL, "NULL handle");
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
+  graphs_clear(h);
   if (!V) {
     for (void* q : {(void*)h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]})
       if (q) cudaFree(q);
@@ -1622,7 +1638,44 @@ wp_status wp_step(wp_handle* h, int64_t nsteps) {
   if (nsteps == 0) return WP_OK;
   wp_status st = run_set_step(h, h->host_step);
   if (st != WP_OK) return st;
-  return WP_DISPATCH(h, chunk_seq<T>(h, nsteps, false));
+  if (!h->graphs_on || h->profiling || !h->stream) return WP_DISPATCH(h, chunk_seq<T>(h, nsteps, false));
+  // a chunk length seen before runs as a CUDA graph: its launches read the step index and
+  // the potential from device memory, so a replay is the same chunk at the current time
+  if (h->graph_seen[nsteps] == 0) {
+    h->graph_seen[nsteps]++;
+    return WP_DISPATCH(h, chunk_seq<T>(h, nsteps, false));
+  }
+  auto it = h->graphs.find(nsteps);
+  if (it == h->graphs.end()) {
+    const int64_t save = h->host_step;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "begin capture");
+    st = WP_DISPATCH(h, chunk_seq<T>(h, nsteps, false));
+    e = cudaStreamEndCapture(h->stream, &g);
+    h->host_step = save;
+    if (st != WP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "graph instantiate");
+    it = h->graphs.emplace(nsteps, ex).first;
+  }
+  WP_CUDA(h, cudaGraphLaunch(it->second, h->stream));
+  h->host_step += nsteps;
+  return WP_OK;
+}
+
+wp_status wp_set_graphs(wp_handle* h, int enable) {
+  if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  if (enable && !h->stream) return fail(h, WP_EINVAL, "graphs need a stream other than the legacy default stream");
+  graphs_clear(h);
+  h->graphs_on = enable != 0;
+  return WP_OK;
 }
 
 wp_status wp_observe(wp_handle* h, wp_obs* out) {
@@ -1758,6 +1811,7 @@ int64_t wp_launch_count(const wp_handle* h) { return h ? h->launches : 0; }
 
 wp_status wp_profile_enable(wp_handle* h, int enable) {
   if (!h) return fail(h, WP_EINVAL, "NULL handle");
+  graphs_clear(h);
   h->profiling = enable != 0;
   return WP_OK;
 }

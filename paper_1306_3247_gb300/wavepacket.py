@@ -114,6 +114,7 @@ def load_library(build_if_missing: bool = True):
         "wp_expect_grid": ([H, vp, ctypes.c_int, P(ctypes.c_double)], ctypes.c_int),
         "wp_run_callback": ([H, ctypes.c_int64, ctypes.c_int64, RECORD_FN, vp, P(ctypes.c_int64)], ctypes.c_int),
         "wp_set_potential_source": ([H, ctypes.c_char_p], ctypes.c_int),
+        "wp_set_graphs": ([H, ctypes.c_int], ctypes.c_int),
         "wp_get_schedule": ([H, P(WpSchedule)], ctypes.c_int),
         "wp_set_schedule": ([H, P(WpSchedule)], ctypes.c_int),
         "wp_autotune": ([H, ctypes.c_int32, P(WpSchedule), P(ctypes.c_double), P(ctypes.c_int32)], ctypes.c_int),
@@ -217,6 +218,11 @@ def wp_set_potential(h, pot: WpPotential):
 def wp_set_potential_grid(h, ptr, on_device: bool):
     lib = load_library()
     _check(lib, h, lib.wp_set_potential_grid(h, ctypes.c_void_p(ptr or 0), 1 if on_device else 0))
+
+
+def wp_set_graphs(h, enable: bool):
+    lib = load_library()
+    _check(lib, h, lib.wp_set_graphs(h, 1 if enable else 0))
 
 
 def wp_expect_grid(h, ptr: int, on_device: bool) -> float:
@@ -437,6 +443,10 @@ class Propagator:
             if a.shape != self.shape:
                 raise ValueError(f"grid shape {a.shape} != {self.shape}")
             wp_set_potential_grid(self.h, a.ctypes.data, False)
+
+    def set_graphs(self, enable: bool):
+        """CUDA-graph replay of repeated step(n) calls (needs a stream)."""
+        wp_set_graphs(self.h, enable)
 
     def expect_grid(self, A) -> float:
         """<psi|A|psi> for a position-space operator on the grid (numpy or CUDA tensor)."""
