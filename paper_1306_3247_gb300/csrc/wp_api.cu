@@ -436,6 +436,8 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.Wst = tb[axis].Wst;
   p.fixed = pl.fixed ? 1 : 0;
   p.max_radix_log = pl.max_radix_log;
+  p.sep = 0;
+  for (int k = 0; k < h->hpot.nterms; k++) p.sep |= h->hpot.term[k].shape != WP_SHAPE_GAUSS;
   for (int d = 0; d < h->ndim; d++) {
     p.K[d] = khalf ? tb[d].Khalf : tb[d].Kfull;
     p.K_lo[d] = khalf ? tb[d].Khalf_lo : tb[d].Kfull_lo;

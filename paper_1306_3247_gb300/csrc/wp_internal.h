@@ -172,6 +172,7 @@ struct PassParams {
   const void* Wst;     // per-stage twiddle records of the pass axis
   int32_t fixed;       // use the fixed-size kernel (n = 2^logn, 2048-element tiles)
   int32_t max_radix_log;  // largest butterfly of the run-time-shape kernel (2 or 3)
+  int32_t sep;            // the potential has additive (non-Gaussian) terms: apply the P factors
   const cx<T>* K[3];
   const cx<T>* K_lo[3];
   const cx<T>* P[3];

@@ -831,7 +831,8 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
         const int i = i0 + k * ISTEP;
         cx<T> v = s[i * LS + l];
         if (ph) {
-          v = apply_factor_rec(v, p.Prec[i], rec.L);
+          // without additive terms the factors are exactly 1 and the product is skipped
+          if (p.sep) v = apply_factor_rec(v, p.Prec[i], rec.L);
           if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
           if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
           s[i * LS + l] = v;
@@ -887,7 +888,7 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
       const int l = e & (C - 1), i = e >> logC;
       cx<T> v = s[i * LS + l];
       if (f & F_PHASE) {
-        v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
+        if (p.sep) v = apply_factor(v, Pa[i], Pal[i], sLh[l], sLl[l]);
         for (int gg = 0; gg < p.ngauss; gg++) v = apply_gauss_phase(v, sGl[gg][l] * p.G[gg][p.axis][i]);
         if (p.grid_rec) v = tw_apply<false>(v, p.grid_rec[tile_gidx(p, sh, o0, cb, i, l)]);
         s[i * LS + l] = v;
