@@ -495,12 +495,16 @@ __device__ __forceinline__ cx<float> apply_factor(cx<float> v, cx<float> ah, cx<
 
 // exp(-i theta) applied to v. In FP32 the factor is written as 1 + (c - 1) - i s with
 // c - 1 = -2 sin^2(theta/2), whose modulus is 1 up to O(eps theta^2).
-// FP64: for |theta| < 1/16 (the usual barrier phase per step) the Taylor series of sin and
-// cos to theta^9 / theta^10 is exact to below 1e-20 relative and costs a dozen FMAs;
-// larger arguments use the library sincos.
+// FP64: Taylor series of sin and cos, to theta^5 / theta^6 for |theta| < 2^-8 (below
+// 1e-18 relative; the usual barrier phase per step) and to theta^9 / theta^10 for
+// |theta| < 1/16 (below 1e-20); larger arguments use the library sincos.
 __device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th) {
   double sn, cs;
-  if (fabs(th) < 0.0625) {
+  if (fabs(th) < 0.00390625) {
+    const double z = th * th;
+    sn = th * (1.0 + z * (-1.0 / 6 + z * (1.0 / 120)));
+    cs = 1.0 + z * (-0.5 + z * (1.0 / 24 + z * (-1.0 / 720)));
+  } else if (fabs(th) < 0.0625) {
     const double z = th * th;
     sn = th * (1.0 + z * (-1.0 / 6 + z * (1.0 / 120 + z * (-1.0 / 5040 + z * (1.0 / 362880)))));
     cs = 1.0 + z * (-0.5 + z * (1.0 / 24 + z * (-1.0 / 720 + z * (1.0 / 40320 + z * (-1.0 / 3628800)))));
