@@ -513,11 +513,16 @@ __device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th)
   }
   return cmul(v, mk(cs, -sn));
 }
-// Float-float: the same Taylor series in float-float arithmetic for |theta| < 1/16, the
-// FP64 sincos otherwise.
+// Float-float: the same two Taylor tiers in float-float arithmetic, the FP64 sincos
+// otherwise.
 __device__ __forceinline__ cx<ff> apply_gauss_phase(cx<ff> v, ff th) {
   ff sn, cs;
-  if (fabsf(th.hi) < 0.0625f) {
+  if (fabsf(th.hi) < 0.00390625f) {
+    // |theta| < 2^-8: terms to theta^5 / theta^6 (below 1e-18 relative)
+    const ff z = th * th;
+    sn = th * (ff(1.0) + z * (ff(-1.0 / 6) + z * ff(1.0 / 120)));
+    cs = ff(1.0) + z * (ff(-0.5) + z * (ff(1.0 / 24) + z * ff(-1.0 / 720)));
+  } else if (fabsf(th.hi) < 0.0625f) {
     const ff z = th * th;
     sn = th * (ff(1.0) + z * (ff(-1.0 / 6) + z * (ff(1.0 / 120) + z * (ff(-1.0 / 5040) + z * ff(1.0 / 362880)))));
     cs = ff(1.0) + z * (ff(-0.5) + z * (ff(1.0 / 24) + z * (ff(-1.0 / 720) + z * (ff(1.0 / 40320) +
