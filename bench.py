@@ -49,10 +49,11 @@ FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate measured on this machine's GB300 (profile
 # ncu capture of the current kernels (profiles/pass_kernels_256cube_all_forms.md). Valid
 # for grid 256 only; any other grid reports null.
 TRAFFIC_256 = {
-    "c128": {"pass_contig": 477851904, "pass_strided": 472023040, "pass_kinetic": 477815296},
-    "c64": {"pass_contig": 210352896, "pass_strided": 209572864, "pass_kinetic": 214511872},
-    "c128f": {"pass_contig": 478671616, "pass_strided": 471820288, "pass_kinetic": 477283328},
+    "c128": {"pass_contig": 478631168, "pass_strided": 471776256, "pass_kinetic": 477397760},
+    "c64": {"pass_contig": 210424576, "pass_strided": 209548032, "pass_kinetic": 214138368},
+    "c128f": {"pass_contig": 478746624, "pass_strided": 471871488, "pass_kinetic": 477539840},
 }
+
 
 def traffic_of(grid, precision, kernel_class):
     return TRAFFIC_256.get(precision, {}).get(kernel_class) if grid == 256 else None
