@@ -499,6 +499,9 @@ __device__ __forceinline__ cx<float> apply_factor(cx<float> v, cx<float> ah, cx<
 // 1e-18 relative; the usual barrier phase per step) and to theta^9 / theta^10 for
 // |theta| < 1/16 (below 1e-20); larger arguments use the library sincos.
 __device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th) {
+  // a localised term leaves most points with |theta| < 2^-60, where the factor is 1 to
+  // below 1e-18 relative: those points are left as they are
+  if (fabs(th) < 0x1p-60) return v;
   double sn, cs;
   if (fabs(th) < 0.00390625) {
     const double z = th * th;
@@ -516,6 +519,7 @@ __device__ __forceinline__ cx<double> apply_gauss_phase(cx<double> v, double th)
 // Float-float: the same two Taylor tiers in float-float arithmetic, the FP64 sincos
 // otherwise.
 __device__ __forceinline__ cx<ff> apply_gauss_phase(cx<ff> v, ff th) {
+  if (fabsf(th.hi) < 0x1p-56f) return v;  // the factor is 1 to below the pair's precision
   ff sn, cs;
   if (fabsf(th.hi) < 0.00390625f) {
     // |theta| < 2^-8: terms to theta^5 / theta^6 (below 1e-18 relative)
@@ -538,6 +542,7 @@ __device__ __forceinline__ cx<ff> apply_gauss_phase(cx<ff> v, ff th) {
 __device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {
   float sh, ch;
   const float h = 0.5f * th;
+  if (fabsf(h) < 0x1p-26f) return v;  // v g is below half an ulp of v
   if (fabsf(h) < 0.03125f) {
     // Taylor series of sin and cos at h (terms to h^7 / h^6 leave < 1e-15 relative)
     const float z = h * h;
