@@ -3,6 +3,8 @@
 // units wp_batch_*.cu, which compile in parallel.
 #pragma once
 
+#include <mutex>
+
 #include "wp_kernels.cuh"
 
 namespace wp {
@@ -11,13 +13,13 @@ namespace batch_detail {
 template <class T, bool CONTIG, int LOGN>
 int launch_cls(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t block_off,
                int64_t nblocks, uint32_t flags, int khalf, size_t smem, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(k_pass_batch<T, CONTIG, LOGN>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    if (e != cudaSuccess) return (int)e;
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    attr = cudaFuncSetAttribute(k_pass_batch<T, CONTIG, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                64 * 1024);
+  });
+  if (attr != cudaSuccess) return (int)attr;
   if (nblocks > 0)
     k_pass_batch<T, CONTIG, LOGN><<<(unsigned)nblocks, 256, smem, st>>>(params, tile_start, block_inst, block_off,
                                                                         flags, khalf);

@@ -2,6 +2,8 @@
 // per-precision translation units).
 #pragma once
 
+#include <mutex>
+
 #include "wp_kernels.cuh"
 
 namespace wp {
@@ -180,13 +182,15 @@ int launch_prep_batch(const PrepParams<T>* params, int ninst, int step_add, doub
 template <class T>
 int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept, int64_t nsteps, size_t smem,
                        void* stream) {
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_res1d_batch<T, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_res1d_batch<T, 16, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_res1d_batch<T, 16, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  std::call_once(once, [] {
+    const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    attr = cudaFuncSetAttribute(k_res1d_batch<T, 8, 256>, a, 200 * 1024);
+    if (attr == cudaSuccess) attr = cudaFuncSetAttribute(k_res1d_batch<T, 16, 512>, a, 200 * 1024);
+    if (attr == cudaSuccess) attr = cudaFuncSetAttribute(k_res1d_batch<T, 16, 1024>, a, 200 * 1024);
+  });
+  if (attr != cudaSuccess) return (int)attr;
   if (ninst <= 0) return 0;
   cudaStream_t st = (cudaStream_t)stream;
   if (ept == 8 && nthreads <= 256)
