@@ -46,6 +46,18 @@ __device__ __forceinline__ ff operator+(ff a, ff b) {
   return ff_fast_renorm(s, e);
 }
 
+// Sum without the final renormalisation: s = fl(a.hi + b.hi) and the exact error of that
+// sum plus the low parts, left as an unnormalised pair (|lo| a few ulp of hi). Inside a
+// butterfly, whose adds feed only further adds and the final renormalisation (ff_norm),
+// this keeps the same precision and drops three operations per sum.
+__device__ __forceinline__ ff ff_add_raw(ff a, ff b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ff_make(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_norm(ff a) { return ff_fast_renorm(a.hi, a.lo); }
+
 __device__ __forceinline__ ff operator-(ff a) { return ff_make(-a.hi, -a.lo); }
 
 __device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }

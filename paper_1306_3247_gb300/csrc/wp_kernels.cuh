@@ -87,13 +87,53 @@ __device__ __forceinline__ double to_f64(ff v) { return (double)v; }
 // ------------------------------------------------------------------ butterflies
 // DFT of length R in registers, natural order in and out:
 // X_k = sum_r x_r exp(-+ 2 pi i r k / R) (minus forward, plus inverse).
+// Butterfly sums: the plain sums, and for float-float the unnormalised ones (cnorm
+// renormalises the outputs of a butterfly).
+template <class T>
+__device__ __forceinline__ cx<T> cadd_b(cx<T> a, cx<T> b) {
+  return cadd(a, b);
+}
+template <class T>
+__device__ __forceinline__ cx<T> csub_b(cx<T> a, cx<T> b) {
+  return csub(a, b);
+}
+template <class T>
+__device__ __forceinline__ cx<T> cnorm(cx<T> a) {
+  return a;
+}
+template <>
+__device__ __forceinline__ cx<ff> cadd_b<ff>(cx<ff> a, cx<ff> b) {
+  return mk(ff_add_raw(a.re, b.re), ff_add_raw(a.im, b.im));
+}
+template <>
+__device__ __forceinline__ cx<ff> csub_b<ff>(cx<ff> a, cx<ff> b) {
+  return mk(ff_add_raw(a.re, -b.re), ff_add_raw(a.im, -b.im));
+}
+template <>
+__device__ __forceinline__ cx<ff> cnorm<ff>(cx<ff> a) {
+  return mk(ff_norm(a.re), ff_norm(a.im));
+}
+
+__device__ __forceinline__ float radd(float a, float b) { return a + b; }
+__device__ __forceinline__ double radd(double a, double b) { return a + b; }
+__device__ __forceinline__ ff radd(ff a, ff b) { return ff_add_raw(a, b); }
+
+template <class T, bool INV>
+__device__ __forceinline__ void dft4_b(cx<T>& x0, cx<T>& x1, cx<T>& x2, cx<T>& x3) {
+  cx<T> a0 = cadd_b(x0, x2), a1 = csub_b(x0, x2), a2 = cadd_b(x1, x3), a3 = rot<T, INV>(csub_b(x1, x3));
+  x0 = cadd_b(a0, a2);
+  x2 = csub_b(a0, a2);
+  x1 = cadd_b(a1, a3);
+  x3 = csub_b(a1, a3);
+}
+
 template <class T, bool INV>
 __device__ __forceinline__ void dft4(cx<T>& x0, cx<T>& x1, cx<T>& x2, cx<T>& x3) {
-  cx<T> a0 = cadd(x0, x2), a1 = csub(x0, x2), a2 = cadd(x1, x3), a3 = rot<T, INV>(csub(x1, x3));
-  x0 = cadd(a0, a2);
-  x2 = csub(a0, a2);
-  x1 = cadd(a1, a3);
-  x3 = csub(a1, a3);
+  dft4_b<T, INV>(x0, x1, x2, x3);
+  x0 = cnorm(x0);
+  x1 = cnorm(x1);
+  x2 = cnorm(x2);
+  x3 = cnorm(x3);
 }
 
 template <class T, int R, bool INV>
@@ -138,23 +178,23 @@ template <class T, bool INV>
 struct Dft<T, 8, INV> {
   static __device__ __forceinline__ void run(cx<T>* v) {
     // radix-2 split into even and odd radix-4 transforms, combined with w8^k
-    dft4<T, INV>(v[0], v[2], v[4], v[6]);
-    dft4<T, INV>(v[1], v[3], v[5], v[7]);
+    dft4_b<T, INV>(v[0], v[2], v[4], v[6]);
+    dft4_b<T, INV>(v[1], v[3], v[5], v[7]);
     cx<T> o1 = v[3], o2 = v[5], o3 = v[7];
-    cx<T> t1 = INV ? mk(mul_rsqrt2(o1.re - o1.im), mul_rsqrt2(o1.re + o1.im))
-                   : mk(mul_rsqrt2(o1.re + o1.im), mul_rsqrt2(o1.im - o1.re));
+    cx<T> t1 = INV ? mk(mul_rsqrt2(radd(o1.re, -o1.im)), mul_rsqrt2(radd(o1.re, o1.im)))
+                   : mk(mul_rsqrt2(radd(o1.re, o1.im)), mul_rsqrt2(radd(o1.im, -o1.re)));
     cx<T> t2 = rot<T, INV>(o2);
-    cx<T> t3 = INV ? mk(-mul_rsqrt2(o3.re + o3.im), mul_rsqrt2(o3.re - o3.im))
-                   : mk(mul_rsqrt2(o3.im - o3.re), -mul_rsqrt2(o3.re + o3.im));
+    cx<T> t3 = INV ? mk(-mul_rsqrt2(radd(o3.re, o3.im)), mul_rsqrt2(radd(o3.re, -o3.im)))
+                   : mk(mul_rsqrt2(radd(o3.im, -o3.re)), -mul_rsqrt2(radd(o3.re, o3.im)));
     cx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, t1);
-    v[5] = csub(e1, t1);
-    v[2] = cadd(e2, t2);
-    v[6] = csub(e2, t2);
-    v[3] = cadd(e3, t3);
-    v[7] = csub(e3, t3);
+    v[0] = cnorm(cadd_b(e0, o0));
+    v[4] = cnorm(csub_b(e0, o0));
+    v[1] = cnorm(cadd_b(e1, t1));
+    v[5] = cnorm(csub_b(e1, t1));
+    v[2] = cnorm(cadd_b(e2, t2));
+    v[6] = cnorm(csub_b(e2, t2));
+    v[3] = cnorm(cadd_b(e3, t3));
+    v[7] = cnorm(csub_b(e3, t3));
   }
 };
 
