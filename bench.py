@@ -49,7 +49,7 @@ FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate measured on this machine's GB300 (profile
 # ncu capture of the current kernels (profiles/pass_kernels_256cube_all_forms.md). Valid
 # for grid 256 only; any other grid reports null.
 TRAFFIC_256 = {
-    "c128": {"pass_contig": 478233600, "pass_strided": 471815168, "pass_kinetic": 477536768},
+    "c128": {"pass_contig": 479680256, "pass_strided": 471920640, "pass_kinetic": 477102848},
     "c64": {"pass_contig": 210324480, "pass_strided": 209497344, "pass_kinetic": 214499840},
     "c128f": {"pass_contig": 478073088, "pass_strided": 471793664, "pass_kinetic": 477358336},
 }

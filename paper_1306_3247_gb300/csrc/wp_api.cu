@@ -11,8 +11,10 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
+#include "wp_fft_f64.h"
 #include "wp_ff.cuh"
 #include "wp_internal.h"
 
@@ -301,7 +303,10 @@ wp_status alloc_tables(wp_handle* h) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
     for (int k = 0; k < 4; k++) off_lo[d][k] = add(n * sizeof(cx<T>));
-    off_st[d] = add(n * 16);
+    int logn = 0;
+    while (((size_t)1 << logn) < n) logn++;
+    // FP64: the fused multiply-add records of both directions (wp_fft_f64.h) follow
+    off_st[d] = add(n * 16 + (std::is_same<T, double>::value ? 2 * (size_t)wp_fma_dir_bytes(logn) : 0));
     for (int k = 0; k < 3; k++) off_rec[d][k] = add(n * sizeof(TwE<T>));
     for (int gg = 0; gg < WP_MAX_GAUSS; gg++) off[d][4 + gg] = add(n * sizeof(T));
     off[d][4 + WP_MAX_GAUSS] = add(n * sizeof(double));
@@ -352,6 +357,14 @@ wp_status alloc_tables(wp_handle* h) {
     split();
     WP_CUDA(h, cudaMemcpy(tb[d].W, hi.data(), nb, cudaMemcpyHostToDevice));
     WP_CUDA(h, cudaMemcpy(tb[d].W_lo, lo.data(), nb, cudaMemcpyHostToDevice));
+    if (std::is_same<T, double>::value) {
+      // FP64: the fused multiply-add records of both directions, after the n 16-byte
+      // entries of the product form
+      const int logn = h->g.ln[d];
+      std::vector<unsigned char> rec(2 * (size_t)wp_fma_dir_bytes(logn));
+      wp_fma_build_tables(logn, rec.data());
+      WP_CUDA(h, cudaMemcpy((char*)tb[d].Wst + n * 16, rec.data(), rec.size(), cudaMemcpyHostToDevice));
+    }
     {
       // per-stage twiddle records for the fixed-size kernels: 16 bytes each, high part
       // then (FP32 only) low part

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <mutex>
+#include <type_traits>
 
 #include "wp_kernels.cuh"
 
@@ -13,16 +14,21 @@ namespace batch_detail {
 template <class T, bool CONTIG, int LOGN>
 int launch_cls(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int64_t block_off,
                int64_t nblocks, uint32_t flags, int khalf, size_t smem, cudaStream_t st) {
+  // the FP64 kernels of compile-time shape have their own register bound
+  constexpr auto kern = [] {
+    if constexpr (std::is_same<T, double>::value && LOGN > 0)
+      return &k_pass_batch_f64<CONTIG, LOGN>;
+    else
+      return &k_pass_batch<T, CONTIG, LOGN>;
+  }();
   static std::once_flag once;
   static cudaError_t attr = cudaSuccess;
   std::call_once(once, [] {
-    attr = cudaFuncSetAttribute(k_pass_batch<T, CONTIG, LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                64 * 1024);
+    attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
   });
   if (attr != cudaSuccess) return (int)attr;
   if (nblocks > 0)
-    k_pass_batch<T, CONTIG, LOGN><<<(unsigned)nblocks, 256, smem, st>>>(params, tile_start, block_inst, block_off,
-                                                                        flags, khalf);
+    kern<<<(unsigned)nblocks, 256, smem, st>>>(params, tile_start, block_inst, block_off, flags, khalf);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : (int)e;
 }

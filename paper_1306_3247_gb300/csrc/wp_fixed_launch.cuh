@@ -4,18 +4,29 @@
 // GRID the one that applies a static grid potential (contiguous passes only).
 #pragma once
 
+#include <type_traits>
+
 #include "wp_kernels.cuh"
 
 namespace wp {
 namespace fixed_detail {
 
+// The kernel of a shape: the FP64 one has its own register bound.
+template <class T, int LOGN, bool CONTIG, bool OBS, bool GRID>
+constexpr auto kernel_of() {
+  if constexpr (std::is_same<T, double>::value)
+    return &k_pass_fixed_f64<LOGN, CONTIG, OBS, GRID>;
+  else
+    return &k_pass_fixed<T, LOGN, CONTIG, OBS, GRID>;
+}
+
 template <class T, bool OBS, bool GRID, int LOGN>
 cudaError_t launch_n(const PassParams<T>& p, unsigned ntiles, size_t smem, cudaStream_t st) {
   if (p.log_inner == 0) {
-    k_pass_fixed<T, LOGN, true, OBS, GRID><<<ntiles, 256, smem, st>>>(p);
+    kernel_of<T, LOGN, true, OBS, GRID>()<<<ntiles, 256, smem, st>>>(p);
   } else {
     if constexpr (GRID) return cudaErrorInvalidConfiguration;
-    else k_pass_fixed<T, LOGN, false, OBS><<<ntiles, 256, smem, st>>>(p);
+    else kernel_of<T, LOGN, false, OBS, false>()<<<ntiles, 256, smem, st>>>(p);
   }
   return cudaGetLastError();
 }
@@ -23,9 +34,9 @@ cudaError_t launch_n(const PassParams<T>& p, unsigned ntiles, size_t smem, cudaS
 template <class T, bool OBS, bool GRID, int LOGN>
 cudaError_t set_limit(int smem) {
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_pass_fixed<T, LOGN, true, OBS, GRID>, a, smem);
+  cudaError_t e = cudaFuncSetAttribute(kernel_of<T, LOGN, true, OBS, GRID>(), a, smem);
   if constexpr (!GRID)
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_pass_fixed<T, LOGN, false, OBS>, a, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel_of<T, LOGN, false, OBS, false>(), a, smem);
   return e;
 }
 

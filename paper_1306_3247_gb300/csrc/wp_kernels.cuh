@@ -14,6 +14,9 @@
 #include <cmath>
 #include <cstdint>
 
+#include <type_traits>
+
+#include "wp_fft_f64.h"
 #include "wp_ff.cuh"
 #include "wp_internal.h"
 
@@ -378,11 +381,66 @@ __device__ __forceinline__ void stage_fixed(cx<T>* s, const TwE<T>* __restrict__
   __syncthreads();
 }
 
-template <class T, int LOGN, int LOGC, int LS, bool INV, int LOGNS, int EPT = 8>
+// The FP64 stages in fused multiply-add form (wp_fft_f64.h): the same loads, stores and
+// stage plan; the butterflies read their twiddle records from the direction's table.
+template <int LOGN, int LOGC, int LS, int LOGNS, bool INV, int EPT = 8>
+__device__ __forceinline__ void stage_fixed_f64(cx<double>* s, const unsigned char* __restrict__ tab, int tid) {
+  constexpr int LR = wp_stage_radix_log(LOGN, LOGNS);
+  constexpr int R = 1 << LR;
+  constexpr int C = 1 << LOGC;
+  constexpr int NR = 1 << (LOGN - LR);
+  constexpr int NT = (C << LOGN) / EPT;  // threads: EPT elements each
+  constexpr int B = EPT / R;
+  constexpr int NS = 1 << LOGNS;
+  constexpr int OFF = (INV ? wp_fma_dir_bytes(LOGN) : 0) + wp_fma_stage_offset(LOGN, LOGNS);
+  constexpr int RB = wp_fma_rec_bytes(LR);
+  cx<double> v[B][R];
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * NT;
+    const int l = bi & (C - 1), j = bi >> LOGC;
+#pragma unroll
+    for (int r = 0; r < R; r++) v[b][r] = s[(j + r * NR) * LS + l];
+    if constexpr (LOGNS == 0) {
+      if constexpr (R == 8)
+        fma_dft8_first<INV>(v[b]);
+      else
+        Dft<double, R, INV>::run(v[b]);
+    } else {
+      const unsigned char* rec = tab + OFF + (j & (NS - 1)) * RB;
+      if constexpr (R == 8)
+        fma_dft8<INV>(v[b], *reinterpret_cast<const Fma8*>(rec));
+      else if constexpr (R == 4)
+        fma_dft4<INV>(v[b], *reinterpret_cast<const Fma4*>(rec));
+      else
+        fma_dft2<INV>(v[b], *reinterpret_cast<const Fma2*>(rec));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < B; b++) {
+    const int bi = tid + b * NT;
+    const int l = bi & (C - 1), j = bi >> LOGC;
+    const int d0 = ((j >> LOGNS) << (LOGNS + LR)) + (j & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; r++) s[(d0 + (r << LOGNS)) * LS + l] = v[b][r];
+  }
+  __syncthreads();
+}
+
+// tw: the per-stage records of the axis, 2^LOGN 16-byte entries; for FP64 the fused
+// multiply-add records of both directions follow them. FMA: use those (FP64 only; the
+// resident 1-D lines keep the product form, whose register needs fit their blocks).
+template <class T, int LOGN, int LOGC, int LS, bool INV, int LOGNS, int EPT = 8,
+          bool FMA = std::is_same<T, double>::value>
 __device__ __forceinline__ void fft_fixed(cx<T>* s, const TwE<T>* __restrict__ tw, int tid) {
   if constexpr (LOGNS < LOGN) {
-    stage_fixed<T, LOGN, LOGC, LS, LOGNS, INV, EPT>(s, tw + wp_stage_tw_offset(LOGN, LOGNS), tid);
-    fft_fixed<T, LOGN, LOGC, LS, INV, LOGNS + wp_stage_radix_log(LOGN, LOGNS), EPT>(s, tw, tid);
+    if constexpr (FMA)
+      stage_fixed_f64<LOGN, LOGC, LS, LOGNS, INV, EPT>(s, reinterpret_cast<const unsigned char*>(tw + (1 << LOGN)),
+                                                       tid);
+    else
+      stage_fixed<T, LOGN, LOGC, LS, LOGNS, INV, EPT>(s, tw + wp_stage_tw_offset(LOGN, LOGNS), tid);
+    fft_fixed<T, LOGN, LOGC, LS, INV, LOGNS + wp_stage_radix_log(LOGN, LOGNS), EPT, FMA>(s, tw, tid);
   }
 }
 
@@ -1105,10 +1163,10 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
 // instance's parameters to shared memory and runs the pass body: LOGN = 6..10 the
 // compile-time-shape body (with per-line records), LOGN = 0 the run-time one.
 template <class T, bool CONTIG, int LOGN>
-__global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
-                                                    const int64_t* __restrict__ tile_start,
-                                                    const int* __restrict__ block_inst, int64_t block_off,
-                                                    uint32_t flags, int khalf) {
+__device__ __forceinline__ void pass_batch_body(const PassParams<T>* __restrict__ params,
+                                                const int64_t* __restrict__ tile_start,
+                                                const int* __restrict__ block_inst, int64_t block_off, uint32_t flags,
+                                                int khalf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
   PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
@@ -1178,6 +1236,23 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
   }
 }
 
+template <class T, bool CONTIG, int LOGN>
+__global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restrict__ params,
+                                                    const int64_t* __restrict__ tile_start,
+                                                    const int* __restrict__ block_inst, int64_t block_off,
+                                                    uint32_t flags, int khalf) {
+  pass_batch_body<T, CONTIG, LOGN>(params, tile_start, block_inst, block_off, flags, khalf);
+}
+// FP64 with a compile-time shape (LOGN = 6..10): at most 64 registers, so that four
+// blocks share an SM (the FP64 pipe needs the warps to cover its latency).
+template <bool CONTIG, int LOGN>
+__global__ void __launch_bounds__(256, 4) k_pass_batch_f64(const PassParams<double>* __restrict__ params,
+                                                          const int64_t* __restrict__ tile_start,
+                                                          const int* __restrict__ block_inst, int64_t block_off,
+                                                          uint32_t flags, int khalf) {
+  pass_batch_body<double, CONTIG, LOGN>(params, tile_start, block_inst, block_off, flags, khalf);
+}
+
 template <class T>
 __device__ void lines_body(const LinesParams<T>& p);
 
@@ -1199,6 +1274,15 @@ template <class T, int LOGN, bool CONTIG, bool OBS, bool GRID = false>
 __global__ void __launch_bounds__(256) k_pass_fixed(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pass_body<T, 8, OBS, FixShape<LOGN, CONTIG>, GRID>(p, FixShape<LOGN, CONTIG>(), reinterpret_cast<cx<T>*>(smem_raw));
+}
+// FP64: at most 64 registers, so that four blocks share an SM (the FP64 pipe needs the
+// warps to cover its latency); the passes that also form observable sums or apply a grid
+// potential, at most 80 (three blocks).
+template <int LOGN, bool CONTIG, bool OBS, bool GRID = false>
+__global__ void __launch_bounds__(256, (OBS || GRID) ? 3 : 4) k_pass_fixed_f64(const PassParams<double> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_body<double, 8, OBS, FixShape<LOGN, CONTIG>, GRID>(p, FixShape<LOGN, CONTIG>(),
+                                                          reinterpret_cast<cx<double>*>(smem_raw));
 }
 
 // ------------------------------------------------------------------ per-line records
@@ -1377,7 +1461,7 @@ struct Res1dFix {
   __device__ explicit Res1dFix(const Res1dParams<T>&) {}
   template <class T, bool INV>
   __device__ __forceinline__ void fft(cx<T>* s, const Res1dParams<T>& p, int tid) const {
-    fft_fixed<T, LOGN, 0, 1, INV, 0, EPT>(s, reinterpret_cast<const TwE<T>*>(p.Wst), tid);
+    fft_fixed<T, LOGN, 0, 1, INV, 0, EPT, false>(s, reinterpret_cast<const TwE<T>*>(p.Wst), tid);
   }
 };
 
