@@ -1,5 +1,6 @@
 // FP64 Stockham butterflies in fused multiply-add form, for the fixed-size transforms of
-// the complex128 path (the FFT steps of Eq. 9 and Algorithm 1 of arXiv:1306.3247).
+// the complex128 path (the Fourier transforms of eq. (ft), Sec. 2.1, and Algorithm 1 of
+// arXiv:1306.3247).
 //
 // GB300 runs FP64 at 1/58 of its FP32 rate, so the complex128 passes are bound by the
 // FP64 pipe, where an add costs as much as a fused multiply-add. A twiddled butterfly

@@ -1,8 +1,9 @@
 """The FP64 fused multiply-add butterflies and their twiddle records (wp_fft_f64.h),
 compiled for the host with the Stockham stage order and index map of the fixed-size
-device transform (tests/fft_f64_host.cpp), against numpy's FFT: the DFT of Eq. 9's
-transforms, X_k = sum_j x_j exp(-+ 2 pi i j k / n), forward and inverse (unnormalised),
-for every length the fixed-size kernels take and the shorter ones."""
+device transform (tests/fft_f64_host.cpp), against numpy's FFT: the DFT behind the
+Fourier transforms of eq. (ft) (Sec. 2.1), X_k = sum_j x_j exp(-+ 2 pi i j k / n),
+forward and inverse (unnormalised), for every length the fixed-size kernels take and the
+shorter ones."""
 import os
 import shutil
 import struct
