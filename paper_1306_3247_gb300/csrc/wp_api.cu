@@ -362,8 +362,10 @@ wp_status alloc_tables(wp_handle* h) {
       // entries of the product form
       const int logn = h->g.ln[d];
       std::vector<unsigned char> rec(2 * (size_t)wp_fma_dir_bytes(logn));
-      wp_fma_build_tables(logn, rec.data());
-      WP_CUDA(h, cudaMemcpy((char*)tb[d].Wst + n * 16, rec.data(), rec.size(), cudaMemcpyHostToDevice));
+      if (!rec.empty()) {
+        wp_fma_build_tables(logn, rec.data());
+        WP_CUDA(h, cudaMemcpy((char*)tb[d].Wst + n * 16, rec.data(), rec.size(), cudaMemcpyHostToDevice));
+      }
     }
     {
       // per-stage twiddle records for the fixed-size kernels: 16 bytes each, high part

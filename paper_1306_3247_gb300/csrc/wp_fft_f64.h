@@ -234,6 +234,7 @@ WP_HD void fma_dft8_first(cx<double>* v) {
 inline void wp_fma_build_tables(int logn, unsigned char* out) {
   const long double pi = 3.141592653589793238462643383279502884L;
   const int dir = wp_fma_dir_bytes(logn);
+  if (dir == 0) return;  // n <= 8: no twiddled stage
   memset(out, 0, 2 * (size_t)dir);
   for (int inv = 0; inv < 2; inv++) {
     int ls = 0;
