@@ -47,6 +47,8 @@ MUTANTS = {
                               "double v = orc_potential_at(p, nterms, terms, x, t);"),
     "grid_dropped_in_energy": ("sv += (orc_potential_at(p, nterms, terms, x, t) + (p->vgrid ? p->vgrid[idx] : 0.0)) * rho;",
                                "sv += orc_potential_at(p, nterms, terms, x, t) * rho;"),
+    "autocorr_overlap_with_current_state": ("cplx c = conj(psi0[idx]) * psi[idx];",
+                                            "cplx c = conj(psi[idx]) * psi[idx];"),
 }
 
 PIN_TESTS = [
@@ -62,6 +64,7 @@ PIN_TESTS = [
     lambda: PINS.test_constant_grid_potential_is_a_global_phase("vkv"),
     lambda: PINS.test_harmonic_grid_potential_ground_state_3d(),
     lambda: PINS.test_morse_eigenstates_energy_and_stationarity(),
+    lambda: PINS.test_free_gaussian_autocorrelation_closed_form_1d("vkv"),
 ]
 
 

@@ -96,6 +96,48 @@ def test_free_gaussian_closed_form_3d_anisotropic():
     assert rel_l2(psi, ref) < 1e-11
 
 
+def free_gaussian_autocorr(t, p0, sigma, m, hbar):
+    """|<psi(0)|psi(t)>|^2 of a free Sec. 4.2 packet along one axis. Its wavenumber is
+    normally distributed, mean k0 = p0/hbar and variance 1/sigma^2 (position std sigma/2),
+    and the free evolution multiplies each wavenumber component by exp(-i a k^2) with
+    a = hbar t / 2m, so the overlap is the characteristic function of a noncentral
+    chi-square: (1 + 2 i a s2)^(-1/2) exp(-i a k0^2 / (1 + 2 i a s2)), s2 = 1/sigma^2.
+    Its squared modulus is (1 + 4 a^2 s2^2)^(-1/2) exp(-4 a^2 s2 k0^2 / (1 + 4 a^2 s2^2))."""
+    s2 = 1.0 / (sigma * sigma)
+    k0 = p0 / hbar
+    a = hbar * t / (2.0 * m)
+    q = 1.0 + 4.0 * a * a * s2 * s2
+    return q ** -0.5 * math.exp(-4.0 * a * a * s2 * k0 * k0 / q)
+
+
+@pytest.mark.parametrize("order", ["vkv", "kvk"])
+def test_free_gaussian_autocorrelation_closed_form_1d(order):
+    # Tab. 3 autocorrelation |<psi(0)|psi(t)>|^2 at t > 0: a moving, spreading packet whose
+    # overlap with psi(0) falls from 1 to 0.096 by t = 1 (ground states would stay at 1)
+    pb = {"ndim": 1, "n": [1024], "xmin": [-20.0], "L": [40.0], "mass": 1.0, "hbar": 1.0,
+          "dt": 0.01, "t0": 0.0, "order": order}
+    psi0 = O.gaussian(pb, [-5.0], [2.0], [1.0])
+    _, obs = O.run(pb, [], psi0, 100, 20)
+    assert len(obs) == 6 and obs[-1, 14] < 0.1
+    for rec in obs:
+        assert abs(rec[14] - free_gaussian_autocorr(rec[0], 2.0, 1.0, 1.0, 1.0)) < 1e-12, rec[0]
+
+
+def test_free_gaussian_autocorrelation_closed_form_3d_anisotropic():
+    # the overlap of a product state is the product of the per-axis overlaps; different
+    # n, L, mass, hbar, p0 and sigma per axis, and a nonzero t0
+    pb = {"ndim": 3, "n": [64, 64, 128], "xmin": [-12.0, -12.0, -16.0], "L": [24.0, 24.0, 32.0],
+          "mass": 1.7, "hbar": 0.8, "dt": 0.04, "t0": 0.3, "order": "kvk"}
+    x0, p0, sg = [-1.0, 0.5, 2.0], [1.2, -0.7, 0.0], [1.6, 1.9, 1.3]
+    psi0 = O.gaussian(pb, x0, p0, sg)
+    _, obs = O.run(pb, [], psi0, 30, 10)
+    for rec in obs:
+        t = rec[0] - pb["t0"]
+        ref = math.prod(free_gaussian_autocorr(t, p0[d], sg[d], 1.7, 0.8) for d in range(3))
+        assert abs(rec[14] - ref) < 1e-12, t
+    assert obs[-1, 14] < 0.8
+
+
 @pytest.mark.parametrize("j", [3, 64 - 5, 32])
 def test_plane_wave_kinetic_phase_and_momentum(j):
     # psi = exp(i k_j x) with k_j from the FFT ordering (j >= n/2 is negative; n/2 is Nyquist)
