@@ -306,23 +306,37 @@ int32_t wp_server_running(const wp_server* s);
 wp_status wp_server_destroy(wp_server* s);
 const char* wp_server_last_error(const wp_server* s);
 
+/* Arithmetic-rate probe. The paper has no counterpart of this call. It measures the
+ * fused multiply-add throughput of the current device in TFLOP/s (one FMA = 2 FLOPs):
+ * fp64 != 0 for FP64, 0 for FP32, with 8 independent FMA chains per thread in 8 blocks
+ * of 256 threads per SM, timed with CUDA events on `stream` (NULL = legacy default)
+ * around the second of two launches of about 0.1 s each. The native FP64 form of the
+ * split step is bound by the FP64 rate on GB300, so this is the peak its roofline
+ * fraction is stated against. Synchronises the stream. Errors: WP_EINVAL (NULL
+ * tflops), WP_ECUDA. */
+wp_status wp_probe_fma_rate(int32_t fp64, void* stream, double* tflops);
+
 /* Allocation-free moments. The paper has no counterpart of this call: it exists for
  * callers that cannot call cudaMalloc (a host application whose device memory is held
  * by its own pool or reserved up front, code in a callback where allocation is not
  * allowed, a loop that cannot take the synchronisation an allocation may cause).
- * Computes norm, <x_d> and <x_d^2> (Tab. 3 definitions, FP64 sums) of a caller-owned
- * complex128 row-major state psi_dev on the grid of `problem`, and writes them to the
- * host record *out (other fields 0, t = problem->t0). It allocates nothing: the partial
- * sums go to a fixed 256 KiB device array inside the library, present on every device
- * that loads it until the process exits. Limit: at most 16,777,216 grid points (e.g.
- * 256^3); larger grids return WP_EUNSUPPORTED with a message naming the limit.
- * The first call on a device (with that device current) looks up the array's device
- * address; make that first call before any stream capture. Every call shares the one
+ * Computes, with FP64 sums over the grid of `problem` (cell volume dV = prod dx_d,
+ * x_d = xmin_d + i dx_d), the moments of a caller-owned complex128 row-major state
+ * psi_dev: norm = sqrt(sum |psi|^2 dV), x[d] = sum x_d |psi|^2 dV and
+ * x2[d] = sum x_d^2 |psi|^2 dV, written to the host record *out (other fields 0,
+ * t = problem->t0). It allocates nothing: the partial sums go to a fixed 256 KiB device
+ * array inside the library, present on every device that loads it until the process
+ * exits. Limit: at most 16,777,216 grid points (e.g. 256^3); larger grids return
+ * WP_EUNSUPPORTED with a message naming the limit. The first call on a device (with
+ * that device current) looks up the array's device address. Every call shares the one
  * array and overwrites it (no slot needs to start at zero), so calls whose kernels
  * overlap on the GPU (different streams or host threads) race: serialise them.
- * Runs on `stream` (NULL = legacy default) and synchronises it before returning.
+ * Runs on `stream` (NULL = legacy default), copies the record into pageable host memory
+ * and synchronises the stream before returning, so it cannot be called on a stream that
+ * is being captured into a CUDA graph.
  * Errors: WP_EINVAL (NULL argument, extent < 1), WP_EUNSUPPORTED (too many points),
- * WP_ECUDA; the message is in wp_moments_noalloc_error(). */
+ * WP_ECUDA (a failed launch, copy or synchronisation); the message of the calling
+ * thread's last failure is in wp_moments_noalloc_error(). */
 wp_status wp_moments_noalloc(const wp_problem* problem, const void* psi_dev, void* stream, wp_obs* out);
 const char* wp_moments_noalloc_error(void);
 

@@ -108,7 +108,9 @@ __global__ void __launch_bounds__(kThreads) k_moments_final(MomentGeom g, int nb
 
 std::mutex g_setup_mutex;
 void* g_scratch_addr[64] = {};  // device address of g_moment_scratch, per device ordinal
-std::string g_noalloc_err;
+// The last error message of the calling thread: a call on another thread never replaces
+// (and so never frees) the string a caller is reading.
+thread_local std::string g_noalloc_err;
 
 wp_status noalloc_fail(wp_status st, const std::string& msg) {
   g_noalloc_err = msg;
@@ -161,8 +163,16 @@ wp_status wp_moments_noalloc(const wp_problem* problem, const void* psi_dev, voi
     scratch = (double*)g_scratch_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
+  // Clear an earlier, non-sticky launch error so that the checks below see only this
+  // call's launches; a launch that fails (no kernel image for the device, a stream of
+  // another device) must not let the copy below return the previous call's record.
+  (void)cudaGetLastError();
   k_moments_partial<<<(unsigned)nblocks, kThreads, 0, st>>>((const double2*)psi_dev, g, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(WP_ECUDA, std::string("moments launch: ") + cudaGetErrorString(e));
   k_moments_final<<<1, kThreads, 0, st>>>(g, (int)nblocks, scratch);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(WP_ECUDA, std::string("moments launch: ") + cudaGetErrorString(e));
   double rec[kSlots];
   e = cudaMemcpyAsync(rec, scratch + (int64_t)kMaxBlocks * kSlots, sizeof(rec), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

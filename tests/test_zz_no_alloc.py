@@ -2,7 +2,9 @@
 
 It is for callers that cannot allocate device memory; its scratch is a fixed device
 array inside the library. Two calls in a row on the same state must agree with the
-handle's own observables (wp_observe, which uses allocated scratch) to FP64 rounding.
+handle's own observables (wp_observe, which uses allocated scratch) to FP64 rounding,
+up to the documented limit of 16,777,216 points (256^3), where every block slot of the
+fixed array is in use and the record sits right after the last one.
 This file is collected last so that a failure here comes after every other test.
 """
 import ctypes
@@ -43,8 +45,9 @@ def _check(o, ref, ndim):
         assert abs(o.x2[d] - ref["xx%d" % d]) <= RTOL * abs(ref["xx%d" % d])
 
 
-@pytest.mark.parametrize("cfg", [W.config_1d_driven_trap(), W.config_3d_barrier(n=64), W.config_2d_laser_trap(n=256)],
-                         ids=["1d", "3d", "2d"])
+@pytest.mark.parametrize("cfg", [W.config_1d_driven_trap(), W.config_3d_barrier(n=64), W.config_2d_laser_trap(n=256),
+                                 W.config_3d_barrier(n=256)],
+                         ids=["1d", "3d", "2d", "3d_256_at_the_limit"])
 def test_noalloc_moments_match_observe_twice(cfg):
     lib = _lib()
     pb = cfg["problem"]
