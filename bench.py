@@ -43,10 +43,8 @@ from paper_1306_3247_gb300 import workloads as W  # noqa: E402
 
 METRIC = "grid-point·steps/s (256³ c128 plain vs batched c64) + served p50/p99 ms"
 UNIT = "grid-point·steps/s"
-FP64_PEAK_TFLOPS = 1.199  # FP64 FMA rate measured on this machine's GB300 (profiles/gb300_alu_rates.md)
-
 # DRAM bytes (read + write) per launch of each pass class on the 256^3 workload, from one
-# ncu capture of the current kernels (profiles/pass_kernels_256cube_all_forms.md). Valid
+# ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum). Valid
 # for grid 256 only; any other grid reports null.
 TRAFFIC_256 = {
     "c128": {"pass_contig": 479680256, "pass_strided": 471920640, "pass_kinetic": 477102848},
@@ -188,6 +186,19 @@ def reference_arm(args, world, rank):
                              "sample": f"one Strang step of the {args.grid}^3 barrier workload per bench step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def probe_rate(WPK, fp64):
+    """FMA throughput of the device in TFLOP/s, measured by the library's probe."""
+    import ctypes
+    lib = WPK.load_library()
+    lib.wp_probe_fma_rate.argtypes = [ctypes.c_int32, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.wp_probe_fma_rate.restype = ctypes.c_int
+    out = ctypes.c_double(0.0)
+    st = lib.wp_probe_fma_rate(1 if fp64 else 0, None, ctypes.byref(out))
+    if st != WPK.WP_OK:
+        raise RuntimeError("wp_probe_fma_rate failed with status %d" % st)
+    return out.value
 
 
 def pass_flops_per_point(logn, kind):
@@ -371,6 +382,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=120)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="run the default schedule instead of the autotuned one")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="time only the uneven-instance batch (complex64) and print its record")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
@@ -381,6 +394,12 @@ def main():
     from paper_1306_3247_gb300 import wavepacket as WPK
 
     torch.cuda.set_device(local)
+    if args.batch_only:
+        r = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=args.steps, warmup=args.warmup,
+                          plain_subset=0, autotune=args.autotune)
+        if rank == 0:
+            print(json.dumps({"batched": r}))
+        return
     head = bench_3d(args, WPK, args.precision, world, local, args.steps, args.warmup, args.nt, with_e2e=True,
                     with_clocks=True, keep_state=(args.precision == "c128" and not args.no_extra and rank == 0))
     ref_state = head.pop("state", None)
@@ -392,11 +411,15 @@ def main():
     avg_s = dom_v["avg_ms"] / 1e3
     elem = 8 if args.precision == "c64" else 16
     if args.precision == "c128":
+        fp64_peak = probe_rate(WPK, True)
+        fp32_peak = probe_rate(WPK, False)
         flops = pass_flops_per_point(logn, dom_name) * npts
-        roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / FP64_PEAK_TFLOPS,
+        roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / fp64_peak,
                 "traffic": traffic_of(args.grid, args.precision, dom_name),
-                "peak_source": "FP64 FMA rate measured on the box (profiles/gb300_alu_rates.md)",
+                "peak_source": "FP64 FMA rate measured in this run by wp_probe_fma_rate (8 independent FMA "
+                               "chains per thread, 8 blocks of 256 threads per SM, CUDA events)",
+                "fp32_fma_tflops": fp32_peak,
                 "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"],
                 "hbm_frac": 2 * npts * elem / avg_s / 1e9 / pk["hbm_gbs"]}
     else:
@@ -421,10 +444,10 @@ def main():
             r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
             st = r.pop("state", None)
             if st is not None and ref_state is not None:
-                # error of the form against the native FP64 result of the same job (which
-                # the parity tests pin to the FP64 oracle)
-                r["rel_l2_vs_fp64"] = float(torch.linalg.vector_norm(st - ref_state) /
-                                            torch.linalg.vector_norm(ref_state))
+                # error of the form against the native FP64 GPU result of the same job; the
+                # parity tests compare every form with the FP64 CPU oracle on this job
+                r["rel_l2_vs_native_fp64_gpu"] = float(torch.linalg.vector_norm(st - ref_state) /
+                                                       torch.linalg.vector_norm(ref_state))
             extra.setdefault("forms", {})[form] = r
         # the paper's K-V-K order (eq. splitop, Algorithm 1) on the same job, native FP64
         r = bench_3d(args, WPK, "c128", 1, local, args.steps, 1, args.nt, with_e2e=False, order="kvk")
