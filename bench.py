@@ -43,6 +43,10 @@ from paper_1306_3247_gb300 import workloads as W  # noqa: E402
 
 METRIC = "grid-point·steps/s (256³ c128 plain vs batched c64) + served p50/p99 ms"
 UNIT = "grid-point·steps/s"
+# FP64 operations per clock per SM on GB300: 2 FP64 fused multiply-adds (the nominal
+# 1.25 TFLOP/s over 152 SMs at 2070 MHz).
+FP64_FLOP_PER_CLOCK_PER_SM = 4
+
 # DRAM bytes (read + write) per launch of each pass class on the 256^3 workload, from one
 # ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum). Valid
 # for grid 256 only; any other grid reports null.
@@ -411,15 +415,18 @@ def main():
     avg_s = dom_v["avg_ms"] / 1e3
     elem = 8 if args.precision == "c64" else 16
     if args.precision == "c128":
-        fp64_peak = probe_rate(WPK, True)
-        fp32_peak = probe_rate(WPK, False)
+        # the FP64 pipe bounds this form: peak derived from the unit counts and the clock
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = pk.get("sm_max_mhz") or 2070.0
+        fp64_peak = nsm * FP64_FLOP_PER_CLOCK_PER_SM * mhz * 1e6 / 1e12
         flops = pass_flops_per_point(logn, dom_name) * npts
         roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / fp64_peak,
                 "traffic": traffic_of(args.grid, args.precision, dom_name),
-                "peak_source": "FP64 FMA rate measured in this run by wp_probe_fma_rate (8 independent FMA "
-                               "chains per thread, 8 blocks of 256 threads per SM, CUDA events)",
-                "fp32_fma_tflops": fp32_peak,
+                "peak_source": f"derived: {nsm} SMs x 2 FP64 FMA per clock x 2 FLOP x {mhz:.0f} MHz "
+                               "(GB300 nominal FP64 1.25 TFLOP/s)",
+                "probe_fp64_fma_tflops": probe_rate(WPK, True),
+                "probe_fp32_fma_tflops": probe_rate(WPK, False),
                 "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"],
                 "hbm_frac": 2 * npts * elem / avg_s / 1e9 / pk["hbm_gbs"]}
     else:

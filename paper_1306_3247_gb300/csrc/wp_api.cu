@@ -109,6 +109,14 @@ namespace {
 
 std::string g_err;  // message for failures before a handle exists
 
+// The smallest power of two >= v (1 for v <= 0 or not finite).
+double pow2_at_least(double v) {
+  if (!(v > 0.0) || !std::isfinite(v)) return 1.0;
+  int e = 0;
+  const double m = std::frexp(v, &e);  // v = m 2^e, 0.5 <= m < 1
+  return m == 0.5 ? std::ldexp(1.0, e - 1) : std::ldexp(1.0, e);
+}
+
 wp_status fail(wp_handle* h, wp_status st, const std::string& msg) {
   if (h)
     h->err = msg;
@@ -299,6 +307,7 @@ wp_status alloc_tables(wp_handle* h) {
   size_t off_st[3];
   size_t off_rec[3][3];
   size_t off_obs[3][3];
+  size_t off_w256[3] = {0, 0, 0};
   for (int d = 0; d < h->ndim; d++) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
@@ -314,6 +323,7 @@ wp_status alloc_tables(wp_handle* h) {
     off_obs[d][0] = add(n * sizeof(cx<T>));
     off_obs[d][1] = add(n * sizeof(cx<T>));
     off_obs[d][2] = add(n * sizeof(T));
+    off_w256[d] = (std::is_same<T, float>::value && n == 256) ? add(256 * 16) : 0;
   }
   WP_CUDA(h, cudaMalloc(&h->tabmem, bytes));
   WP_CUDA(h, cudaMemsetAsync(h->tabmem, 0, bytes, h->stream));
@@ -339,6 +349,7 @@ wp_status alloc_tables(wp_handle* h) {
     tb[d].Ox = (cx<T>*)(base + off_obs[d][0]);
     tb[d].Ok = (cx<T>*)(base + off_obs[d][1]);
     tb[d].AT = (T*)(base + off_obs[d][2]);
+    tb[d].W256 = (std::is_same<T, float>::value && h->n[d] == 256) ? (void*)(base + off_w256[d]) : nullptr;
   }
   // static tables (high and low parts)
   for (int d = 0; d < h->ndim; d++) {
@@ -394,6 +405,17 @@ wp_status alloc_tables(wp_handle* h) {
       }
       WP_CUDA(h, cudaMemcpy(tb[d].Wst, rec.data(), rec.size(), cudaMemcpyHostToDevice));
     }
+    if (tb[d].W256) {
+      // two-stage 256-point kernels: exp(-2 pi i t k1/256) at k1 * 16 + t, high + low parts
+      std::vector<TwE<float>> w(256);
+      const long double pi = 3.141592653589793238462643383279502884L;
+      for (int k1 = 0; k1 < 16; k1++)
+        for (int t = 0; t < 16; t++) {
+          const long double a = -2.0L * pi * (long double)((t * k1) % 256) / 256.0L;
+          w[k1 * 16 + t] = make_rec<float>((double)cosl(a), (double)sinl(a));
+        }
+      WP_CUDA(h, cudaMemcpy(tb[d].W256, w.data(), w.size() * sizeof(TwE<float>), cudaMemcpyHostToDevice));
+    }
     {
       // coordinates and wavenumbers (and their squares) of the axis, rounded to T
       std::vector<cx<T>> ox(n), ok(n);
@@ -401,8 +423,9 @@ wp_status alloc_tables(wp_handle* h) {
         const double x = h->g.xmin[d] + (double)i * h->g.dx[d];
         const int64_t js = (int64_t)i < (int64_t)(n / 2) ? (int64_t)i : (int64_t)i - (int64_t)n;
         const double k = h->g.kscale[d] * (double)js;
-        ox[i] = cx<T>{(T)x, (T)(x * x)};
-        ok[i] = cx<T>{(T)k, (T)(k * k)};
+        const double xs = x / h->g.oscale_x[d], ks = k / h->g.oscale_k[d];
+        ox[i] = cx<T>{(T)xs, (T)(xs * xs)};
+        ok[i] = cx<T>{(T)ks, (T)(ks * ks)};
       }
       WP_CUDA(h, cudaMemcpy(tb[d].Ox, ox.data(), nb, cudaMemcpyHostToDevice));
       WP_CUDA(h, cudaMemcpy(tb[d].Ok, ok.data(), nb, cudaMemcpyHostToDevice));
@@ -481,6 +504,7 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.AT = tb[axis].AT;
   p.grid_v = h->vgrid;
   p.grid_rec = (h->vgrid && h->phase_half >= 0) ? (const TwE<T>*)h->vgrid_rec[h->phase_half] : nullptr;
+  p.W256 = tb[axis].W256;
   return p;
 }
 
@@ -1178,10 +1202,16 @@ wp_status batch_compile(wp_batch* b) {
     std::vector<int> bz, bx;
     auto order = [&](int axis, std::vector<int64_t>& ts, std::vector<int>& binst, std::vector<BatchPassClass>& cl) {
       std::map<int, std::vector<int>> by;
+      // complex64 instances whose pass axis has 256 points (fixed schedule) run the
+      // two-stage kernels, as they do alone: 16-line (contiguous) or 16-column tiles
+      auto p256 = [&](const wp_handle* hk) {
+        return std::is_same<T, float>::value && hk->plan[axis].fixed && hk->n[axis] == 256 &&
+               (axis == 1 ? hk->n[0] >= 16 : hk->n[1] >= 16);
+      };
       for (size_t k = 0; k < b->idx2d.size(); k++) {
         const wp_handle* hk = b->inst[b->idx2d[k]];
         // fixed-size class when the instance's schedule uses the fixed kernel, else run-time shape
-        by[hk->plan[axis].fixed ? hk->g.ln[axis] : 0].push_back((int)k);
+        by[p256(hk) ? kBatchClassP256 : (hk->plan[axis].fixed ? hk->g.ln[axis] : 0)].push_back((int)k);
       }
       ts.assign(b->idx2d.size(), 0);
       for (auto& kv : by) {
@@ -1190,7 +1220,8 @@ wp_status batch_compile(wp_batch* b) {
         c.off = (int64_t)binst.size();
         for (int k : kv.second) {
           ts[k] = (int64_t)binst.size();
-          const int64_t nt = b->inst[b->idx2d[k]]->plan[axis].ntiles;
+          const wp_handle* hk = b->inst[b->idx2d[k]];
+          const int64_t nt = kv.first == kBatchClassP256 ? (hk->N >> 12) : hk->plan[axis].ntiles;
           for (int64_t t = 0; t < nt; t++) binst.push_back(k);
         }
         c.n = (int64_t)binst.size() - c.off;
@@ -1408,6 +1439,9 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     g.dx[d] = d < pb->ndim ? pb->L[d] / (double)pb->n[d] : 1.0;
     g.kscale[d] = d < pb->ndim ? 2.0 * 3.14159265358979323846 / pb->L[d] : 0.0;
     if (d < pb->ndim) g.dv *= g.dx[d];
+    const double xm = std::max(std::fabs(g.xmin[d]), std::fabs(g.xmin[d] + (double)(h->n[d] - 1) * g.dx[d]));
+    g.oscale_x[d] = pow2_at_least(xm);
+    g.oscale_k[d] = pow2_at_least(g.kscale[d] * (double)(h->n[d] / 2));
   }
   g.mass = pb->mass;
   g.hbar = pb->hbar;

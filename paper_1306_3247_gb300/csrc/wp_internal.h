@@ -126,6 +126,11 @@ struct Geom {
   double kscale[3];    // 2 pi / L
   double mass, hbar, dt, t0;
   double dv;           // cell volume
+  // Powers of two at or above the largest |x_i| and |k_i| of each axis. The observable
+  // tables of the line sums (Ox, Ok) hold x / oscale_x and k / oscale_k, so that sums
+  // formed in FP32 range stay finite in any units (in SI units k^2 |psi_hat|^2 alone
+  // exceeds the FP32 range); the FP64 combination multiplies the scale back, exactly.
+  double oscale_x[3], oscale_k[3];
 };
 
 // Device tables of one axis for precision T.
@@ -149,6 +154,7 @@ struct AxisTab {
   cx<T>* Ox;                  // (x_i, x_i^2) in T: line sums of the position moments
   cx<T>* Ok;                  // (k_i, k_i^2) in T: line sums of the momentum moments
   T* AT;                      // A(x,t) rounded to T: line sums of the potential energy
+  void* W256;                 // complex64, n = 256: records exp(-2 pi i t k1/256) at k1 * 16 + t
 };
 
 template <class T>
@@ -195,6 +201,7 @@ struct PassParams {
   const T* AT;
   const TwE<T>* grid_rec;  // static grid potential: phase records of this pass's tau, or NULL
   const double* grid_v;    // static grid potential (observables), or NULL
+  const void* W256;        // two-stage 256-point kernels: twiddle records of the pass axis, or NULL
 };
 
 // Per-line records of one pass (k_lines).
@@ -349,6 +356,13 @@ int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);
 // fixed-size pass kernels (their own translation units, wp_fixed_*.cu)
 template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
+// two-stage complex64 kernels for 256-point lines (wp_pass256_f32.cu)
+bool pass256_applies(const PassParams<float>& p);
+int launch_pass256(const PassParams<float>& p, void* stream);
+// their batched form: one launch over a class of blocks (16-line or 16-column tiles)
+constexpr int kBatchClassP256 = 1000;  // class key of those blocks in a batch's block lists
+int launch_pass256_batch(const PassParams<float>* params, const int64_t* tile_start, const int* block_inst,
+                         bool contig, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
 template <class T> int fixed_smem_limit_set(size_t smem);
 // batched pass kernels, contiguous and strided axis (wp_batch_*.cu): one launch per
 // line-length class, blocks block_off .. block_off + nblocks - 1 of the class-sorted list

@@ -838,8 +838,9 @@ __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[
       grid_index(p.g, ax, o0, cb + l, 0, gi);
     if (p.flags & F_OBS_POS) {
       c[Q_RHO] = lt[0];
-      c[Q_X + ax] = lt[1];
-      c[Q_XX + ax] = lt[2];
+      const double xs = p.g.oscale_x[ax];  // the tables hold x / xs
+      c[Q_X + ax] = lt[1] * xs;
+      c[Q_XX + ax] = lt[2] * (xs * xs);
       double A = 0.0;
       for (int d = 0; d < p.g.ndim; d++) {
         if (d == ax) continue;
@@ -860,7 +861,8 @@ __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[
       c[Q_AC_IM] = lt[7];
     } else {
       c[Q_RHOK] = lt[0];
-      c[Q_K + ax] = lt[1];
+      const double ks = p.g.oscale_k[ax];  // the tables hold k / ks
+      c[Q_K + ax] = lt[1] * ks;
       double k2 = 0.0;
       for (int d = 0; d < p.g.ndim; d++) {
         if (d == ax) continue;
@@ -868,7 +870,7 @@ __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[
         c[Q_K + d] = k * lt[0];
         k2 += k * k;
       }
-      c[Q_K2] = lt[2] + k2 * lt[0];
+      c[Q_K2] = lt[2] * (ks * ks) + k2 * lt[0];
     }
   }
   __syncthreads();

@@ -44,6 +44,9 @@ int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* strea
   const bool obs = (p.flags & (F_OBS_POS | F_OBS_MOM)) != 0;
   const dim3 grid((unsigned)ntiles), block(p.nthreads);
   cudaStream_t st = (cudaStream_t)stream;
+  if constexpr (std::is_same<T, float>::value) {
+    if (pass256_applies(p)) return launch_pass256(p, stream);
+  }
   if (p.fixed) {
     if (p.nthreads != 256 || p.logC != 11 - p.logn) return (int)cudaErrorInvalidConfiguration;
     const bool contig = p.log_inner == 0;
@@ -155,6 +158,12 @@ int launch_lines(const LinesParams<T>& p, void* stream) {
 template <class T>
 int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int logn,
                       int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) {
+  // the two-stage complex64 kernels of 256-point lines have a class of their own
+  if constexpr (std::is_same<T, float>::value) {
+    if (logn == kBatchClassP256)
+      return launch_pass256_batch(params, tile_start, block_inst, (flags & F_KIN) == 0, block_off, nblocks, flags,
+                                  khalf, stream);
+  }
   // the contiguous pass carries the potential phase, the strided one the kinetic factor
   if ((flags & F_KIN) == 0)
     return launch_pass_batch_contig<T>(params, tile_start, block_inst, logn, block_off, nblocks, flags, khalf, smem,

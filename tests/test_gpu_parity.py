@@ -56,6 +56,46 @@ def test_fft_matches_oracle(shape, prec):
         assert rel_l2(P.get_state() / x.size, x) < tol
 
 
+# Shapes that run the two-stage complex64 kernels for 256-point lines: the contiguous axis
+# with 16, 32 or 64 lines, and strided axes with 16 or more adjacent columns (the kernels
+# run in complex64 only; complex128 runs the same shapes on the Stockham kernels).
+@pytest.mark.parametrize("shape", [(16, 256), (256, 16), (256, 256), (4, 256, 32), (256, 2, 16), (2, 256, 64)])
+@pytest.mark.parametrize("prec", ["c64", "c128"])
+def test_fft_256_lines_match_oracle(shape, prec):
+    nd = len(shape)
+    pb = {"ndim": nd, "n": list(shape), "xmin": [0.0] * nd, "L": [1.0] * nd, "dt": 0.1}
+    x = W.random_state(shape, seed=7 * sum(shape))
+    tol = {"c128": 1e-13, "c64": 3e-6}[prec]
+    with WPK.Propagator(pb, precision=prec) as P:
+        P.set_state(x)
+        P.fft(-1)
+        assert rel_l2(P.get_state(), O.fft(x, -1)) < tol
+        P.fft(+1)
+        assert rel_l2(P.get_state() / x.size, x) < tol
+
+
+def test_2d_256_square_c64_1000_steps():
+    # 256^2: both axes on the two-stage complex64 kernels (contiguous: IFFT, phase, FFT;
+    # strided: FFT, kinetic factor, IFFT), a Gaussian barrier and a driven trap
+    pb = {"ndim": 2, "n": [256, 256], "xmin": [-16.0, -16.0], "L": [32.0, 32.0], "mass": 1.0, "hbar": 1.0,
+          "dt": 0.005, "t0": 0.0}
+    terms = [{"shape": "quad", "a": [0.25, 0.5], "coef": {"A0": 1.0}},
+             {"shape": "gauss", "a": [1.0, 1.5], "c0": [1.0, 0.0], "coef": {"A0": 1.0, "A": 0.3, "omega": 2.0}},
+             {"shape": "linear", "a": [1.0, 0.0], "coef": {"A": 0.1, "omega": 0.7}}]
+    psi0 = O.gaussian(pb, [-2.0, 0.5], [1.5, 0.0], [1.2, 1.0])
+    ref, ref_obs = O.run(pb, terms, psi0, 1000, 100)
+    with WPK.Propagator(pb, terms, "c64", autocorr=True) as P:
+        P.set_state(psi0)
+        obs = P.run(1000, 100)
+        psi = P.get_state()
+    err = rel_l2(psi, ref)
+    drift = float(np.max(np.abs(obs["norm"] - obs["norm"][0])))
+    print("c64 256^2 rel L2", err, "norm drift", drift)
+    assert err < TOL64
+    assert drift < 1e-5
+    compare_obs(obs, ref_obs, TOL64)
+
+
 # --------------------------------------------------------------------------- 1-D
 @pytest.mark.parametrize("prec", ["c128", "c128f"])
 @pytest.mark.parametrize("order", ["vkv", "kvk"])

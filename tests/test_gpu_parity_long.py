@@ -127,17 +127,19 @@ def compare_obs_si(obs, ref, rtol, mass):
     assert np.max(np.abs(M[:, 11:14] - ref[:, 11:14])) < rtol * escale
 
 
-@pytest.mark.parametrize("prec", ["c128", "c128f"])
+@pytest.mark.parametrize("prec", ["c128", "c128f", "c64"])
 def test_paul_trap_64_cube_si_units_against_oracle(prec):
     """The Ba+ trap of Sec. 4.2 in SI units (hbar = 1.05e-34 J s, m = 2.3e-25 kg,
-    dt = 2 ns) on a 64^3 grid around the packet: 60 steps, records every 10."""
+    dt = 2 ns) on a 64^3 grid around the packet: 60 steps, records every 10. In SI units
+    k^2 |psi_hat|^2 is about 1e45, beyond the FP32 range the complex64 and float-float
+    line sums are formed in: the kernels scale their coordinate and wavenumber tables."""
     cfg = paul_small()
     ref, ref_obs = oracle_run("paul64", cfg, 60, 10)
     psi, obs = gpu_run(cfg, prec, 60, 10)
     err = rel_l2(psi, ref)
     print(f"{prec}: relative L2 against the oracle {err:.3e}")
-    assert err < TOL128
-    compare_obs_si(obs, ref_obs, 1e-10, cfg["problem"]["mass"])
+    assert err < (TOL64 if prec == "c64" else TOL128)
+    compare_obs_si(obs, ref_obs, TOL64 if prec == "c64" else 1e-10, cfg["problem"]["mass"])
 
 
 def verlet_moments(x, p, m, stiff, nt, dt, npr):
