@@ -98,6 +98,10 @@ struct wp_handle {
   bool graphs_on = false;                     // replay wp_step chunks as CUDA graphs
   std::map<int64_t, cudaGraphExec_t> graphs;  // per chunk length
   std::map<int64_t, int> graph_seen;
+  // side stream of the per-step table kernels (2-D and 3-D): they run beside the strided
+  // passes of the previous step; created on first use
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::vector<EventPair> pending;
   std::vector<cudaEvent_t> free_events;
   double prof_ms[K_NCLASSES] = {};
@@ -817,6 +821,41 @@ wp_status momentum_and_reduce(wp_handle* h) {
   return launch_rc(h, launch_reduce(r, h->stream), "reduce kernel");
 }
 
+// The per-step tables (and line records) of the next step, forked onto the side stream
+// after the potential pass that read the current ones, so that they run beside the
+// strided passes; join_tables makes the main stream wait for them before the next
+// potential pass. Without a side stream they run in line.
+template <class T>
+wp_status fork_tables(wp_handle* h, int step_add, double t_shift, double tau, bool lines) {
+  if (!h->side) {
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      (void)cudaGetLastError();
+      if (h->side) cudaStreamDestroy(h->side);
+      if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+      if (h->join_ev) cudaEventDestroy(h->join_ev);
+      h->side = nullptr;
+      h->fork_ev = h->join_ev = nullptr;
+    }
+  }
+  if (!h->side) return run_prep<T>(h, step_add, t_shift, tau, lines);
+  WP_CUDA(h, cudaEventRecord(h->fork_ev, h->stream));
+  WP_CUDA(h, cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+  cudaStream_t main = h->stream;
+  h->stream = h->side;
+  const wp_status st = run_prep<T>(h, step_add, t_shift, tau, lines);
+  h->stream = main;
+  if (st != WP_OK) return st;
+  WP_CUDA(h, cudaEventRecord(h->join_ev, h->side));
+  return WP_OK;
+}
+
+wp_status join_tables(wp_handle* h) {
+  if (h->side) WP_CUDA(h, cudaStreamWaitEvent(h->stream, h->join_ev, 0));
+  return WP_OK;
+}
+
 // m >= 1 steps from a clean state; ends clean. obs_end: record observables at the end.
 template <class T>
 wp_status chunk_seq(wp_handle* h, int64_t m, bool obs_end) {
@@ -840,26 +879,35 @@ wp_status chunk_seq(wp_handle* h, int64_t m, bool obs_end) {
     return WP_OK;
   };
   const uint32_t obsf = obs_end ? (F_OBS_POS | (h->pb.autocorr ? F_AUTOCORR : 0u)) : 0u;
+  // the tables of step k + 1 are formed beside the strided passes of step k
   if (h->pb.order == WP_ORDER_VKV) {
     if ((st = run_prep<T>(h, 0, 0.0, 0.5 * dt, true)) != WP_OK) return st;
     if ((st = run_pass<T>(h, Z, F_PHASE | F_FFT, S, S)) != WP_OK) return st;
-    if ((st = middle(0)) != WP_OK) return st;
     for (int64_t k = 1; k < m; k++) {
-      if ((st = run_prep<T>(h, 1, 0.0, dt, true)) != WP_OK) return st;
-      if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
+      if ((st = fork_tables<T>(h, 1, 0.0, dt, true)) != WP_OK) return st;
       if ((st = middle(0)) != WP_OK) return st;
+      if ((st = join_tables(h)) != WP_OK) return st;
+      if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
     }
-    if ((st = run_prep<T>(h, 1, 0.0, 0.5 * dt, true)) != WP_OK) return st;
+    if ((st = fork_tables<T>(h, 1, 0.0, 0.5 * dt, true)) != WP_OK) return st;
+    if ((st = middle(0)) != WP_OK) return st;
+    if ((st = join_tables(h)) != WP_OK) return st;
     if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | obsf, S, S, h->part_pos)) != WP_OK) return st;
   } else {
     if ((st = run_pass<T>(h, Z, F_FFT, S, S)) != WP_OK) return st;
+    if ((st = fork_tables<T>(h, 0, 0.5 * dt, dt, true)) != WP_OK) return st;
     if ((st = middle(1)) != WP_OK) return st;
     for (int64_t k = 0; k < m; k++) {
-      if ((st = run_prep<T>(h, k == 0 ? 0 : 1, 0.5 * dt, dt, true)) != WP_OK) return st;
+      if ((st = join_tables(h)) != WP_OK) return st;
       if ((st = run_pass<T>(h, Z, F_IFFT | F_PHASE | F_FFT, S, S)) != WP_OK) return st;
+      if (k < m - 1) {
+        if ((st = fork_tables<T>(h, 1, 0.5 * dt, dt, true)) != WP_OK) return st;
+      } else {
+        if ((st = fork_tables<T>(h, 1, 0.0, 0.0, false)) != WP_OK) return st;
+      }
       if ((st = middle(k == m - 1 ? 1 : 0)) != WP_OK) return st;
     }
-    if ((st = run_prep<T>(h, 1, 0.0, 0.0)) != WP_OK) return st;
+    if ((st = join_tables(h)) != WP_OK) return st;
     if ((st = run_pass<T>(h, Z, F_IFFT | obsf, S, S, h->part_pos)) != WP_OK) return st;
   }
   h->host_step += m;
@@ -1218,12 +1266,17 @@ wp_status batch_compile(wp_batch* b) {
         BatchPassClass c;
         c.logn = kv.first;
         c.off = (int64_t)binst.size();
+        int ng = 0, sep = 0;
         for (int k : kv.second) {
           ts[k] = (int64_t)binst.size();
           const wp_handle* hk = b->inst[b->idx2d[k]];
           const int64_t nt = kv.first == kBatchClassP256 ? (hk->N >> 12) : hk->plan[axis].ntiles;
           for (int64_t t = 0; t < nt; t++) binst.push_back(k);
+          ng = std::max(ng, (int)hk->hpot.ngauss);
+          for (int q = 0; q < hk->hpot.nterms; q++) sep |= hk->hpot.term[q].shape != WP_SHAPE_GAUSS;
         }
+        // the two-stage contiguous kernel of the class's potential kind
+        if (kv.first == kBatchClassP256 && axis == 1) c.logn = kBatchClassP256 + 2 * std::min(ng, 2) + sep;
         c.n = (int64_t)binst.size() - c.off;
         cl.push_back(c);
       }
@@ -1514,6 +1567,12 @@ wp_status wp_destroy(wp_handle* h) {
     cudaEventDestroy(ep.b);
   }
   for (auto e : h->free_events) cudaEventDestroy(e);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  if (h->join_ev) cudaEventDestroy(h->join_ev);
   delete h;
   return WP_OK;
 }

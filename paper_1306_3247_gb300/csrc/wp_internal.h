@@ -359,10 +359,13 @@ template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, siz
 // two-stage complex64 kernels for 256-point lines (wp_pass256_f32.cu)
 bool pass256_applies(const PassParams<float>& p);
 int launch_pass256(const PassParams<float>& p, void* stream);
-// their batched form: one launch over a class of blocks (16-line or 16-column tiles)
-constexpr int kBatchClassP256 = 1000;  // class key of those blocks in a batch's block lists
+// their batched form: one launch over a class of blocks (16-line or 16-column tiles).
+// Class keys kBatchClassP256 + v in a batch's block lists, v = 2 x (largest Gaussian-term
+// count) + (any additive terms) for the contiguous pass, 0 for the strided one; variant
+// -1 selects the strided FFT-only kernel.
+constexpr int kBatchClassP256 = 1000;
 int launch_pass256_batch(const PassParams<float>* params, const int64_t* tile_start, const int* block_inst,
-                         bool contig, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
+                         int variant, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
 template <class T> int fixed_smem_limit_set(size_t smem);
 // batched pass kernels, contiguous and strided axis (wp_batch_*.cu): one launch per
 // line-length class, blocks block_off .. block_off + nblocks - 1 of the class-sorted list

@@ -160,8 +160,8 @@ int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, co
                       int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) {
   // the two-stage complex64 kernels of 256-point lines have a class of their own
   if constexpr (std::is_same<T, float>::value) {
-    if (logn == kBatchClassP256)
-      return launch_pass256_batch(params, tile_start, block_inst, (flags & F_KIN) == 0, block_off, nblocks, flags,
+    if (logn >= kBatchClassP256 && logn < kBatchClassP256 + 6)
+      return launch_pass256_batch(params, tile_start, block_inst, logn - kBatchClassP256, block_off, nblocks, flags,
                                   khalf, stream);
   }
   // the contiguous pass carries the potential phase, the strided one the kinetic factor

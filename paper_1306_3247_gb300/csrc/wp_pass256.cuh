@@ -144,9 +144,14 @@ __device__ __forceinline__ void load_twiddles(TwE<float>* s_tw, const void* W256
   for (int k = threadIdx.x; k < kN; k += blockDim.x) dst[k] = __ldg(src + k);
 }
 
-// Potential phase of point i = t + 16 r of a line with record rec (the fixed-size
-// kernels' factors: additive terms as one exact product of the axis and line records,
-// Gaussian terms as exp(-i theta), theta = line coefficient x axis factor).
+// A factor that is the product of a line factor L (the other axes) and an axis factor a
+// is applied as two products, each with the exact high + low parts and one rounding:
+// both roundings are unbiased, so no norm drift builds up over the steps.
+
+// Potential phase of point i = t + 16 r of a line with record rec: additive terms (SEP)
+// as the line factor and the axis records, NG Gaussian terms as exp(-i theta),
+// theta = line coefficient x axis factor.
+template <int NG, bool SEP>
 __device__ __forceinline__ void phase256(const PassParams<float>& p, cx<float> (&v)[16], const LineRec<float>& rec,
                                          int t) {
   const float* G0 = p.G[0][p.axis];
@@ -155,25 +160,35 @@ __device__ __forceinline__ void phase256(const PassParams<float>& p, cx<float> (
   for (int r = 0; r < 16; r++) {
     const int i = t + 16 * r;
     cx<float> x = v[r];
-    if (p.sep) x = apply_factor_rec(x, p.Prec[i], rec.L);
-    if (p.ngauss > 0) x = apply_gauss_phase(x, rec.g[0] * __ldg(G0 + i));
-    if (p.ngauss > 1) x = apply_gauss_phase(x, rec.g[1] * __ldg(G1 + i));
+    if constexpr (SEP) {
+      const TwE<float> a = p.Prec[i];
+      x = cmul2(cmul2(x, rec.L.h, rec.L.l), a.h, a.l);
+    }
+    if constexpr (NG > 0) x = apply_gauss_phase(x, rec.g[0] * __ldg(G0 + i));
+    if constexpr (NG > 1) x = apply_gauss_phase(x, rec.g[1] * __ldg(G1 + i));
     v[r] = x;
   }
 }
 
-// Kinetic round trip of one line: forward FFT, factor, inverse FFT.
+// Kinetic round trip of one line: line factor, forward FFT, axis factor, inverse FFT
+// (the line factor is constant along the line, so it commutes with the transform).
 __device__ __forceinline__ void kinetic256(const PassParams<float>& p, cx<float> (&v)[16], cx<float>* buf,
                                            const TwE<float>* tw, const TwE<float>& L, int t) {
+#pragma unroll
+  for (int r = 0; r < 16; r++) v[r] = cmul2(v[r], L.h, L.l);
   fft256<false>(v, buf, tw, t);
 #pragma unroll
-  for (int r = 0; r < 16; r++) v[r] = apply_factor_rec(v[r], p.Krec[t + 16 * r], L);
+  for (int r = 0; r < 16; r++) {
+    const TwE<float> a = p.Krec[t + 16 * r];
+    v[r] = cmul2(v[r], a.h, a.l);
+  }
   fft256<true>(v, buf, tw, t);
 }
 
 // Contiguous axis: tile b is lines 16 b .. 16 b + 15; warp w serves lines 16 b + 2 w + g.
 // Flags: F_IFFT, F_PHASE, F_FFT (any subset, in that order). v: the thread's 16 points
 // of its line, already loaded by the caller.
+template <int NG, bool SEP>
 __device__ __forceinline__ void contig_body(const PassParams<float>& p, int64_t tile, unsigned char* smem,
                                             cx<float> (&v)[16]) {
   TwE<float>* s_tw = reinterpret_cast<TwE<float>*>(smem);
@@ -189,7 +204,7 @@ __device__ __forceinline__ void contig_body(const PassParams<float>& p, int64_t 
   if (f & F_IFFT) fft256<true>(v, buf, s_tw, t);
   if (f & F_PHASE) {
     const LineRec<float> rec = p.lines_phase[line];
-    phase256(p, v, rec, t);
+    phase256<NG, SEP>(p, v, rec, t);
   }
   if (f & F_FFT) fft256<false>(v, buf, s_tw, t);
   cx<float>* dst = p.out + (line << kLogN) + t;
@@ -268,12 +283,15 @@ __device__ __forceinline__ void strided_body(const PassParams<float>& p, int64_t
   }
 }
 
+// NG Gaussian terms, SEP additive terms in the potential (one kernel per kind keeps the
+// unrolled phase code small).
+template <int NG, bool SEP>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_pass256_contig(const PassParams<float> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the line loads are issued before the twiddle table's (their latencies overlap)
   cx<float> v[16];
   contig_load(p.in, blockIdx.x, v);
-  contig_body(p, blockIdx.x, smem_raw, v);
+  contig_body<NG, SEP>(p, blockIdx.x, smem_raw, v);
 }
 
 template <bool KIN>
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_pass256_strided(const 
 // copies the instance's parameters to shared memory, so the two latencies overlap; the
 // body is the one of the single-instance kernels, so an instance gives the same bits
 // alone and in a batch.
-template <bool CONTIG, bool KIN>
+template <bool CONTIG, bool KIN, int NG = 0, bool SEP = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_pass256_batch(const PassParams<float>* __restrict__ params,
                                                                const int64_t* __restrict__ tile_start,
                                                                const int* __restrict__ block_inst, int64_t block_off,
@@ -329,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_pass256_batch(const Pa
   }
   __syncthreads();
   if constexpr (CONTIG)
-    contig_body(p, tile, smem_raw, v);
+    contig_body<NG, SEP>(p, tile, smem_raw, v);
   else
     strided_body<KIN>(p, o, cb, smem_raw, ld);
 }
