@@ -15,10 +15,11 @@ over all ranks.
   forms   -- the same job in the float-float complex128-accuracy form and in complex64.
   batched -- 4096 uneven 1-D/2-D driven-trap instances advanced together (complex64,
              chunks of 20 steps replayed as CUDA graphs), next to the plain per-instance
-             FP64 form on a subset of the same instances.
-  served  -- a Poisson request stream (1-D/2-D/3-D jobs, complex64) through the
-             continuous-batching server under an 80 GB budget: p50/p99 latency, offered
-             and achieved rates.
+             FP64 form on a seeded sample of 256 of the same instances.
+  served  -- the seeded Poisson request stream (2000 requests of 1-D/2-D/3-D jobs,
+             complex64) through the continuous-batching server under an 80 GB budget:
+             p50/p99 latency, offered and achieved rates; then its first 500 requests
+             offered below the achieved rate.
 
 --impl reference times the FP64 CPU oracle (the checker) on a bounded sample of the
 3-D workload on the host cores. With --gpus N > 1 (torchrun) every rank runs an
@@ -291,8 +292,9 @@ def bench_3d(args, WPK, precision, world, local, steps, warmup, nt, with_e2e=Tru
     return out
 
 
-def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, autotune=True):
-    """The uneven-instance batch: all instances advance `chunk` steps per bench step.
+def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, autotune=True, job_steps=None):
+    """The uneven-instance batch: all instances advance `chunk` steps per graph replay; a
+    bench step is `job_steps` steps (a whole job of job_steps / chunk replays) or one chunk.
     With autotune, one instance of every distinct 1-D shape is tuned first; the cached
     schedules then apply to all instances of that shape. 2-D instances keep the default
     schedule: the batched 2-D passes run the 2048-element-tile kernels, and an instance
@@ -314,32 +316,41 @@ def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, aut
     for c in inst:
         k = B.add(c["problem"], c["terms"])
         B.init_gaussian(k, **c["init"])
+    per = (job_steps // chunk) if job_steps else 1
     for _ in range(warmup):
         B.step(chunk, use_graph=True)
     torch.cuda.synchronize()
     l0 = B.launches
     t0 = time.perf_counter()
-    for _ in range(steps):
+    for _ in range(steps * per):
         B.step(chunk, use_graph=True)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     launches = B.launches - l0
     finite = bool(np.isfinite(B.get_state(0)).all())
     B.close()
-    out = {"value": sum(pts) * chunk * steps / el, "instances": count, "points": int(sum(pts)),
-           "steps_per_bench_step": chunk, "ms_per_bench_step": el / steps * 1e3, "graph_launches_issued": launches,
+    out = {"value": sum(pts) * chunk * per * steps / el, "instances": count, "points": int(sum(pts)),
+           "steps_per_bench_step": chunk * per, "graph_chunk_steps": chunk, "ms_per_bench_step": el / steps * 1e3,
+           "graph_launches_issued": launches,
            "n1d": sum(1 for c in inst if c["problem"]["ndim"] == 1), "finite": finite, "precision": precision,
            "autotuned_shapes": {"x".join(map(str, k)): v for k, v in tuned.items()}}
     if plain_subset <= 0:
         return out
-    # plain per-instance FP64 form on a subset of the same instances, one handle at a time
-    sub = inst[:plain_subset]
+    # The plain per-instance FP64 form on a seeded sample of the same instances: every
+    # instance its own handle, spread over 16 streams so that instances overlap on the
+    # device, chunks replayed as CUDA graphs (two warm-up chunks: direct, then capture).
+    rng = np.random.default_rng(7)
+    pick = sorted(rng.choice(len(inst), size=min(plain_subset, len(inst)), replace=False).tolist())
+    streams = [torch.cuda.Stream() for _ in range(16)]
     handles = []
-    for c in sub:
-        P = WPK.Propagator(c["problem"], c["terms"], "c128")
+    for k, i in enumerate(pick):
+        c = inst[i]
+        P = WPK.Propagator(c["problem"], c["terms"], "c128", stream=streams[k % 16].cuda_stream)
         P.init_gaussian(**c["init"])
-        P.step(chunk)
         handles.append(P)
+    for _ in range(2):
+        for P in handles:
+            P.step(chunk)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for P in handles:
@@ -348,22 +359,27 @@ def bench_batched(WPK, precision, count, chunk, steps, warmup, plain_subset, aut
     el = time.perf_counter() - t0
     for P in handles:
         P.close()
-    out["plain_fp64_per_instance"] = {"value": sum(pts[:plain_subset]) * chunk / el, "instances": plain_subset}
+    out["plain_fp64_per_instance"] = {"value": sum(pts[i] for i in pick) * chunk / el, "instances": len(pick),
+                                      "sample": "seeded random sample of the batch's instances, 16 streams, "
+                                                "CUDA-graph replay"}
     return out
 
 
-def bench_served(WPK, nreq, precision):
+def bench_served(WPK, nreq, precision, nreq_below=500):
     """The seeded Poisson stream at its own rate (200 req/s offered: far above capacity, so
-    latency is mostly queueing), then the same requests with arrivals stretched so that the
-    offered rate sits below the rate achieved at saturation (latency is then service time)."""
+    latency is mostly queueing), then its first nreq_below requests with arrivals stretched
+    so that the offered rate sits below the rate achieved at saturation (latency is then
+    service time)."""
     from paper_1306_3247_gb300 import serving as S
     reqs = W.request_stream()[:nreq]
     summary, _ = S.serve(reqs, budget_bytes=80e9, nslots=32, chunk_steps=50, precision=precision)
     summary["precision"] = precision
     if summary.get("achieved_rate"):
+        sub = reqs[:min(nreq_below, len(reqs))]
         target = 0.7 * summary["achieved_rate"]
-        scale = summary["offered_rate"] / target if summary.get("offered_rate") else 1.0
-        under, _ = S.serve(reqs, budget_bytes=80e9, nslots=32, chunk_steps=50, precision=precision,
+        offered = len(sub) / sub[-1][0] if sub and sub[-1][0] > 0 else None
+        scale = offered / target if offered else 1.0
+        under, _ = S.serve(sub, budget_bytes=80e9, nslots=32, chunk_steps=50, precision=precision,
                            time_scale=max(1.0, scale))
         under["time_scale"] = max(1.0, scale)
         summary["below_capacity"] = under
@@ -383,11 +399,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="headline only (no forms, batch, serving)")
     ap.add_argument("--batch-count", type=int, default=4096)
-    ap.add_argument("--serve-requests", type=int, default=120)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the seeded stream served at its own rate (the first 500 of them also "
+                         "below capacity)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="run the default schedule instead of the autotuned one")
-    ap.add_argument("--batch-only", action="store_true",
-                    help="time only the uneven-instance batch (complex64) and print its record")
+    ap.add_argument("--only", choices=["batch", "serve"], default=None,
+                    help="time only the uneven-instance batch (complex64) or only the served stream, and print "
+                         "its record")
     args = ap.parse_args()
     world, rank, local = dist_init(args)
     if args.impl == "reference":
@@ -398,11 +417,18 @@ def main():
     from paper_1306_3247_gb300 import wavepacket as WPK
 
     torch.cuda.set_device(local)
-    if args.batch_only:
+    if args.only == "batch":
         r = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=args.steps, warmup=args.warmup,
                           plain_subset=0, autotune=args.autotune)
         if rank == 0:
             print(json.dumps({"batched": r}))
+        return
+    if args.only == "serve":
+        t0 = time.perf_counter()
+        r = bench_served(WPK, args.serve_requests, "c64")
+        r["bench_wall_s"] = time.perf_counter() - t0
+        if rank == 0:
+            print(json.dumps({"served": r}))
         return
     head = bench_3d(args, WPK, args.precision, world, local, args.steps, args.warmup, args.nt, with_e2e=True,
                     with_clocks=True, keep_state=(args.precision == "c128" and not args.no_extra and rank == 0))
@@ -440,7 +466,7 @@ def main():
         for form in ("c128f", "c64"):
             if form == args.precision:
                 continue
-            r = bench_3d(args, WPK, form, 1, local, args.steps, 1, args.nt, with_e2e=False,
+            r = bench_3d(args, WPK, form, 1, local, args.steps, args.warmup, args.nt, with_e2e=False,
                          keep_state=ref_state is not None)
             kd = max(r["kernels"].items(), key=lambda kv: kv[1]["launches"] * kv[1]["avg_ms"])
             el = 8 if form == "c64" else 16
@@ -457,11 +483,12 @@ def main():
                                                        torch.linalg.vector_norm(ref_state))
             extra.setdefault("forms", {})[form] = r
         # the paper's K-V-K order (eq. splitop, Algorithm 1) on the same job, native FP64
-        r = bench_3d(args, WPK, "c128", 1, local, args.steps, 1, args.nt, with_e2e=False, order="kvk")
+        r = bench_3d(args, WPK, "c128", 1, local, args.steps, min(args.warmup, 3), args.nt, with_e2e=False,
+                     order="kvk")
         extra["orders"] = {"kvk": {"value": r["value"], "ms_per_job": r["ms_per_job"], "precision": "c128",
                                    "kernels": r["kernels"]}}
-        extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=3, warmup=3,
-                                         plain_subset=64, autotune=args.autotune)
+        extra["batched"] = bench_batched(WPK, "c64", args.batch_count, chunk=20, steps=1, warmup=3,
+                                         plain_subset=256, autotune=args.autotune, job_steps=2000)
         # the same batch in the complex128-accuracy forms (native FP64 and float-float)
         extra["batched_forms"] = {}
         for form in ("c128", "c128f"):

@@ -124,6 +124,15 @@ typedef struct wp_handle wp_handle;
  * stream: a cudaStream_t or NULL. On success *out owns the handle. */
 wp_status wp_create(const wp_problem* problem, void* stream, wp_handle** out);
 
+/* The same, with all device memory of the handle (state, scratch, tables, records)
+ * taken from mem_pool, a cudaMemPool_t of the current device, by stream-ordered
+ * allocations on `stream`; wp_destroy returns it to the pool. A caller that reserves
+ * its device memory up front (a pool whose release threshold keeps it) creates and
+ * destroys handles without cudaMalloc or cudaFree. mem_pool = NULL is wp_create. The
+ * pool must outlive the handle. The paper has no counterpart of this call. Errors as
+ * wp_create (WP_ECUDA when the pool cannot serve an allocation). */
+wp_status wp_create_pooled(const wp_problem* problem, void* stream, void* mem_pool, wp_handle** out);
+
 /* Set the potential (Sec. 3.2.2-3.2.3). Copied; may be called again between steps. */
 wp_status wp_set_potential(wp_handle* h, const wp_potential* pot);
 

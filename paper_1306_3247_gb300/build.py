@@ -19,7 +19,9 @@ SOURCES = ["wp_api.cu", "wp_kernels_f64.cu", "wp_kernels_f32.cu", "wp_kernels_ff
            "wp_batch_f64_contig.cu", "wp_batch_f64_strided.cu", "wp_batch_f32_contig.cu", "wp_batch_f32_strided.cu",
            "wp_batch_ff_contig.cu", "wp_batch_ff_strided.cu", "wp_res1d_f64.cu", "wp_res1d_f32.cu", "wp_res1d_ff.cu",
            "wp_noalloc.cu", "wp_server.cu", "wp_jit.cu", "wp_probe.cu",
-           "wp_pass256_f32.cu"]
+           "wp_pass256_f32.cu", "wp_pass256_ff.cu", "wp_pass2s_f32.cu", "wp_batch_merged_f32_contig.cu", "wp_batch_merged_f32_strided.cu",
+           "wp_batch_merged_f64_contig.cu", "wp_batch_merged_f64_strided.cu", "wp_batch_merged_ff_contig.cu",
+           "wp_batch_merged_ff_strided.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

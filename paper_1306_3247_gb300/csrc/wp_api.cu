@@ -98,6 +98,9 @@ struct wp_handle {
   bool graphs_on = false;                     // replay wp_step chunks as CUDA graphs
   std::map<int64_t, cudaGraphExec_t> graphs;  // per chunk length
   std::map<int64_t, int> graph_seen;
+  // device memory of the handle: from this stream-ordered pool when set (wp_create_pooled),
+  // else cudaMalloc
+  cudaMemPool_t pool = nullptr;
   // side stream of the per-step table kernels (2-D and 3-D): they run beside the strided
   // passes of the previous step; created on first use
   cudaStream_t side = nullptr;
@@ -147,6 +150,24 @@ wp_status cuda_fail(wp_handle* h, cudaError_t e, const char* what) {
     cudaError_t e_ = (call);                               \
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
+
+// Device memory of a handle: cudaMalloc, or with a pool a stream-ordered allocation on
+// the handle's stream that is complete when the call returns (so that the memory can be
+// used from any stream at once, like cudaMalloc's).
+cudaError_t dev_malloc(wp_handle* h, void** p, size_t bytes) {
+  if (!h->pool) return cudaMalloc(p, bytes);
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+// Released after the work already on the handle's stream (pool) or at once (cudaMalloc).
+void dev_free(wp_handle* h, void* p) {
+  if (!p) return;
+  if (h->pool)
+    cudaFreeAsync(p, h->stream);
+  else
+    cudaFree(p);
+}
 
 cudaEvent_t get_event(wp_handle* h) {
   if (!h->free_events.empty()) {
@@ -312,6 +333,7 @@ wp_status alloc_tables(wp_handle* h) {
   size_t off_rec[3][3];
   size_t off_obs[3][3];
   size_t off_w256[3] = {0, 0, 0};
+  size_t off_w2s[3] = {0, 0, 0};
   for (int d = 0; d < h->ndim; d++) {
     const size_t n = (size_t)h->n[d];
     for (int k = 0; k < 4; k++) off[d][k] = add(n * sizeof(cx<T>));
@@ -327,9 +349,10 @@ wp_status alloc_tables(wp_handle* h) {
     off_obs[d][0] = add(n * sizeof(cx<T>));
     off_obs[d][1] = add(n * sizeof(cx<T>));
     off_obs[d][2] = add(n * sizeof(T));
-    off_w256[d] = (std::is_same<T, float>::value && n == 256) ? add(256 * 16) : 0;
+    off_w256[d] = (!std::is_same<T, double>::value && n == 256) ? add(256 * 16) : 0;
+    off_w2s[d] = (std::is_same<T, float>::value && (n == 64 || n == 128)) ? add(256 * 16) : 0;
   }
-  WP_CUDA(h, cudaMalloc(&h->tabmem, bytes));
+  WP_CUDA(h, dev_malloc(h, &h->tabmem, bytes));
   WP_CUDA(h, cudaMemsetAsync(h->tabmem, 0, bytes, h->stream));
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
   char* base = (char*)h->tabmem;
@@ -353,7 +376,9 @@ wp_status alloc_tables(wp_handle* h) {
     tb[d].Ox = (cx<T>*)(base + off_obs[d][0]);
     tb[d].Ok = (cx<T>*)(base + off_obs[d][1]);
     tb[d].AT = (T*)(base + off_obs[d][2]);
-    tb[d].W256 = (std::is_same<T, float>::value && h->n[d] == 256) ? (void*)(base + off_w256[d]) : nullptr;
+    tb[d].W256 = (!std::is_same<T, double>::value && h->n[d] == 256) ? (void*)(base + off_w256[d]) : nullptr;
+    tb[d].W2s = (std::is_same<T, float>::value && (h->n[d] == 64 || h->n[d] == 128)) ? (void*)(base + off_w2s[d])
+                                                                                     : nullptr;
   }
   // static tables (high and low parts)
   for (int d = 0; d < h->ndim; d++) {
@@ -410,15 +435,34 @@ wp_status alloc_tables(wp_handle* h) {
       WP_CUDA(h, cudaMemcpy(tb[d].Wst, rec.data(), rec.size(), cudaMemcpyHostToDevice));
     }
     if (tb[d].W256) {
-      // two-stage 256-point kernels: exp(-2 pi i t k1/256) at k1 * 16 + t, high + low parts
-      std::vector<TwE<float>> w(256);
+      // two-stage 256-point kernels: exp(-2 pi i t k1/256) at k1 * 16 + t (complex64: high +
+      // low parts; float-float: the pair values)
+      std::vector<TwE<T>> w(256);
       const long double pi = 3.141592653589793238462643383279502884L;
       for (int k1 = 0; k1 < 16; k1++)
         for (int t = 0; t < 16; t++) {
           const long double a = -2.0L * pi * (long double)((t * k1) % 256) / 256.0L;
-          w[k1 * 16 + t] = make_rec<float>((double)cosl(a), (double)sinl(a));
+          w[k1 * 16 + t] = make_rec<T>((double)cosl(a), (double)sinl(a));
         }
-      WP_CUDA(h, cudaMemcpy(tb[d].W256, w.data(), w.size() * sizeof(TwE<float>), cudaMemcpyHostToDevice));
+      WP_CUDA(h, cudaMemcpy(tb[d].W256, w.data(), w.size() * sizeof(TwE<T>), cudaMemcpyHostToDevice));
+    }
+    if (tb[d].W2s) {
+      // two-stage 64- and 128-point kernels (n = 8 T): exp(-2 pi i t k1/n) at k1 T + t, then
+      // for n = 128 exp(-2 pi i j/16) at 8 T + j
+      const int nt = (int)(n / 8);  // threads per line
+      std::vector<TwE<float>> w(256);
+      const long double pi = 3.141592653589793238462643383279502884L;
+      for (int k1 = 0; k1 < 8; k1++)
+        for (int t = 0; t < nt; t++) {
+          const long double a = -2.0L * pi * (long double)(t * k1) / (long double)n;
+          w[k1 * nt + t] = make_rec<float>((double)cosl(a), (double)sinl(a));
+        }
+      if (nt == 16)
+        for (int j = 0; j < 8; j++) {
+          const long double a = -2.0L * pi * (long double)j / 16.0L;
+          w[8 * nt + j] = make_rec<float>((double)cosl(a), (double)sinl(a));
+        }
+      WP_CUDA(h, cudaMemcpy(tb[d].W2s, w.data(), w.size() * sizeof(TwE<float>), cudaMemcpyHostToDevice));
     }
     {
       // coordinates and wavenumbers (and their squares) of the axis, rounded to T
@@ -509,6 +553,7 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.grid_v = h->vgrid;
   p.grid_rec = (h->vgrid && h->phase_half >= 0) ? (const TwE<T>*)h->vgrid_rec[h->phase_half] : nullptr;
   p.W256 = tb[axis].W256;
+  p.W2s = tb[axis].W2s;
   return p;
 }
 
@@ -596,10 +641,10 @@ wp_status run_set_step(wp_handle* h, int64_t step) {
 
 wp_status ensure_obs(wp_handle* h, int64_t cap) {
   if (cap <= h->obs_cap) return WP_OK;
-  if (h->obs_dev) cudaFree(h->obs_dev);
+  dev_free(h, h->obs_dev);
   h->obs_dev = nullptr;
   h->obs_cap = 0;
-  WP_CUDA(h, cudaMalloc(&h->obs_dev, (size_t)cap * 16 * sizeof(double)));
+  WP_CUDA(h, dev_malloc(h, (void**)&h->obs_dev, (size_t)cap * 16 * sizeof(double)));
   h->obs_cap = cap;
   return WP_OK;
 }
@@ -626,14 +671,14 @@ wp_status apply_schedule(wp_handle* h, const wp_schedule& sc) {
     if (maxtiles > h->part_cap) {
       WP_CUDA(h, cudaStreamSynchronize(h->stream));
       double *pp = nullptr, *pm = nullptr;
-      cudaError_t e = cudaMalloc(&pp, (size_t)maxtiles * NQ * sizeof(double));
-      if (e == cudaSuccess) e = cudaMalloc(&pm, (size_t)maxtiles * NQ * sizeof(double));
+      cudaError_t e = dev_malloc(h, (void**)&pp, (size_t)maxtiles * NQ * sizeof(double));
+      if (e == cudaSuccess) e = dev_malloc(h, (void**)&pm, (size_t)maxtiles * NQ * sizeof(double));
       if (e != cudaSuccess) {
-        if (pp) cudaFree(pp);
+        dev_free(h, pp);
         return cuda_fail(h, e, "partials allocation");
       }
-      if (h->part_pos) cudaFree(h->part_pos);
-      if (h->part_mom) cudaFree(h->part_mom);
+      dev_free(h, h->part_pos);
+      dev_free(h, h->part_mom);
       h->part_pos = pp;
       h->part_mom = pm;
       h->part_cap = maxtiles;
@@ -1062,7 +1107,7 @@ wp_status gaussian_impl(wp_handle* h, const double* x0, const double* p0, const 
     p.off[d] = p.nsum;
     p.nsum += h->n[d];
   }
-  if (!h->gauss_tab) WP_CUDA(h, cudaMalloc(&h->gauss_tab, (size_t)p.nsum * sizeof(cx<double>)));
+  if (!h->gauss_tab) WP_CUDA(h, dev_malloc(h, &h->gauss_tab, (size_t)p.nsum * sizeof(cx<double>)));
   p.tab = (cx<double>*)h->gauss_tab;
   {
     LaunchScope ls(h, K_AUX);
@@ -1138,6 +1183,10 @@ struct wp_batch {
   cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int64_t ntiles_z = 0, ntiles_x = 0;
   std::vector<BatchPassClass> cls_z, cls_x;  // line-length classes of the two passes
+  // one launch per pass for the Stockham classes, and the classes launched on their own
+  MergedLaunch ml_z{}, ml_x{};
+  std::vector<BatchPassClass> own_z, own_x;
+  size_t smem_merged = 0;  // dynamic shared memory of the merged launches
   size_t smem2d = 0;
   std::map<int64_t, cudaGraphExec_t> graphs;
   std::map<int64_t, int> seen;  // chunk lengths run once without a graph
@@ -1252,14 +1301,26 @@ wp_status batch_compile(wp_batch* b) {
       std::map<int, std::vector<int>> by;
       // complex64 instances whose pass axis has 256 points (fixed schedule) run the
       // two-stage kernels, as they do alone: 16-line (contiguous) or 16-column tiles
+      // (16 lines per tile complex64, 8 float-float)
+      constexpr int64_t kTileLines = std::is_same<T, float>::value ? 16 : 8;
+      // (float-float: the contiguous pass only, as alone)
       auto p256 = [&](const wp_handle* hk) {
-        return std::is_same<T, float>::value && hk->plan[axis].fixed && hk->n[axis] == 256 &&
-               (axis == 1 ? hk->n[0] >= 16 : hk->n[1] >= 16);
+        return !std::is_same<T, double>::value && hk->plan[axis].fixed && hk->n[axis] == 256 &&
+               (axis == 1 ? hk->n[0] >= kTileLines : (std::is_same<T, float>::value && hk->n[1] >= kTileLines));
+      };
+      // complex64 instances whose pass axis has 64 or 128 points run the two-stage kernels
+      // of those lengths (2048-point tiles, as the Stockham ones)
+      auto p2s = [&](const wp_handle* hk) {
+        return std::is_same<T, float>::value && hk->plan[axis].fixed && (hk->n[axis] == 64 || hk->n[axis] == 128) &&
+               hk->N / hk->n[axis] >= 2048 / hk->n[axis];
       };
       for (size_t k = 0; k < b->idx2d.size(); k++) {
         const wp_handle* hk = b->inst[b->idx2d[k]];
         // fixed-size class when the instance's schedule uses the fixed kernel, else run-time shape
-        by[p256(hk) ? kBatchClassP256 : (hk->plan[axis].fixed ? hk->g.ln[axis] : 0)].push_back((int)k);
+        int key = hk->plan[axis].fixed ? hk->g.ln[axis] : 0;
+        if (p256(hk)) key = kBatchClassP256;
+        if (p2s(hk)) key = kBatchClassP2S + 100 * (hk->g.ln[axis] - 6);
+        by[key].push_back((int)k);
       }
       ts.assign(b->idx2d.size(), 0);
       for (auto& kv : by) {
@@ -1270,19 +1331,49 @@ wp_status batch_compile(wp_batch* b) {
         for (int k : kv.second) {
           ts[k] = (int64_t)binst.size();
           const wp_handle* hk = b->inst[b->idx2d[k]];
-          const int64_t nt = kv.first == kBatchClassP256 ? (hk->N >> 12) : hk->plan[axis].ntiles;
+          const int64_t nt = kv.first == kBatchClassP256 ? hk->N / (256 * kTileLines) : hk->plan[axis].ntiles;
           for (int64_t t = 0; t < nt; t++) binst.push_back(k);
           ng = std::max(ng, (int)hk->hpot.ngauss);
           for (int q = 0; q < hk->hpot.nterms; q++) sep |= hk->hpot.term[q].shape != WP_SHAPE_GAUSS;
         }
         // the two-stage contiguous kernel of the class's potential kind
-        if (kv.first == kBatchClassP256 && axis == 1) c.logn = kBatchClassP256 + 2 * std::min(ng, 2) + sep;
+        if ((kv.first == kBatchClassP256 || kv.first == kBatchClassP2S || kv.first == kBatchClassP2S + 100) &&
+            axis == 1)
+          c.logn = kv.first + 2 * std::min(ng, 2) + sep;
         c.n = (int64_t)binst.size() - c.off;
         cl.push_back(c);
       }
     };
     order(1, tz, bz, b->cls_z);
     order(0, tx, bx, b->cls_x);
+    // merged launches: the classes of 64-, 128- and 256-point lines share one grid per pass
+    auto merge = [&](const std::vector<BatchPassClass>& cl, MergedLaunch& ml, std::vector<BatchPassClass>& own) {
+      ml = MergedLaunch{};
+      own.clear();
+      int64_t at = 0;
+      for (const BatchPassClass& c : cl) {
+        const bool two_stage_short = std::is_same<T, float>::value && c.logn >= kBatchClassP2S &&
+                                     c.logn < kBatchClassP2S + 200;
+        const bool in = (c.logn == 6 || c.logn == 7 || c.logn == 8 || two_stage_short) &&
+                        ml.ncls < kMergedMaxClasses;
+        if (!in) {
+          own.push_back(c);
+          continue;
+        }
+        ml.key[ml.ncls] = c.logn;
+        ml.start[ml.ncls] = at;
+        ml.list_off[ml.ncls] = c.off;
+        at += c.n;
+        ml.ncls++;
+      }
+      ml.start[ml.ncls] = at;
+    };
+    merge(b->cls_z, b->ml_z, b->own_z);
+    merge(b->cls_x, b->ml_x, b->own_x);
+    b->smem_merged = b->smem2d;
+    for (const MergedLaunch* ml : {&b->ml_z, &b->ml_x})
+      for (int c = 0; c < ml->ncls; c++)
+        if (ml->key[c] >= kBatchClassP2S) b->smem_merged = std::max(b->smem_merged, kPass2sSmem);
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_z, pz.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_pass_x, px.size() * sizeof(PassParams<T>)));
     WP_CUDA(nullptr, cudaMalloc(&b->d_prep, pp.size() * sizeof(PrepParams<T>)));
@@ -1318,8 +1409,21 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
     return launch_rc(nullptr, launch_lines_batch<T>((const LinesParams<T>*)b->d_lines, n2, b->max_lines, st),
                      "batched line records");
   };
-  auto zpass = [&](uint32_t f) -> wp_status {
-    for (const BatchPassClass& c : b->cls_z) {
+  // One launch per pass over the merged classes (the kinetic one with the next step's
+  // tables as trailing blocks when asked: step increment, time shift, phase length in dt;
+  // tau 0 forms the tables without line records), then any class of its own.
+  auto zmerged = [&](uint32_t f) -> wp_status {
+    if (b->ml_z.ncls > 0) {
+      b->launches++;
+      const wp_status r = launch_rc(
+          nullptr,
+          launch_merged_contig<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, b->d_binst_z, b->ml_z, f, 0,
+                                  (const PrepParams<T>*)b->d_prep, (const LinesParams<T>*)b->d_lines,
+                                  b->smem_merged, st),
+          "batched pass");
+      if (r != WP_OK) return r;
+    }
+    for (const BatchPassClass& c : b->own_z) {
       b->launches++;
       const wp_status r = launch_rc(nullptr,
                                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_z, b->d_tiles_z, b->d_binst_z,
@@ -1329,8 +1433,26 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
     }
     return WP_OK;
   };
-  auto xpass = [&](int khalf) -> wp_status {
-    for (const BatchPassClass& c : b->cls_x) {
+  auto xmerged = [&](int khalf, bool with_prep, int add, double shift, double tau) -> wp_status {
+    MergedLaunch ml = b->ml_x;
+    if (with_prep) {
+      ml.nprep = n2;
+      ml.step_add = add;
+      ml.shift_dt = shift;
+      ml.tau_dt = tau;
+      ml.lines = tau != 0.0;
+    }
+    if (ml.ncls > 0 || ml.nprep > 0) {
+      b->launches++;
+      const wp_status r = launch_rc(
+          nullptr,
+          launch_merged_strided<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, b->d_binst_x, ml, F_KIN, khalf,
+                                   (const PrepParams<T>*)b->d_prep, (const LinesParams<T>*)b->d_lines,
+                                   b->smem_merged, st),
+          "batched pass");
+      if (r != WP_OK) return r;
+    }
+    for (const BatchPassClass& c : b->own_x) {
       b->launches++;
       const wp_status r = launch_rc(nullptr,
                                     launch_pass_batch<T>((const PassParams<T>*)b->d_pass_x, b->d_tiles_x, b->d_binst_x,
@@ -1361,21 +1483,26 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
   }
   if (fork) WP_CUDA(nullptr, cudaEventRecord(b->join_ev, b->side));
   if (n2 > 0) {
+    // per step: the potential pass, and the kinetic pass with the next step's tables,
+    // each one launch for the Stockham classes plus one per class of its own (the order
+    // of tables, potential and kinetic passes is unchanged)
     if (b->order2d == WP_ORDER_VKV) {
-      if ((s2 = prep(0, 0.0, 0.5)) != WP_OK || (s2 = zpass(F_PHASE | F_FFT)) != WP_OK || (s2 = xpass(0)) != WP_OK)
-        return s2;
+      if ((s2 = prep(0, 0.0, 0.5)) != WP_OK || (s2 = zmerged(F_PHASE | F_FFT)) != WP_OK) return s2;
       for (int64_t k = 1; k < m; k++)
-        if ((s2 = prep(1, 0.0, 1.0)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE | F_FFT)) != WP_OK ||
-            (s2 = xpass(0)) != WP_OK)
+        if ((s2 = xmerged(0, true, 1, 0.0, 1.0)) != WP_OK || (s2 = zmerged(F_IFFT | F_PHASE | F_FFT)) != WP_OK)
           return s2;
-      if ((s2 = prep(1, 0.0, 0.5)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE)) != WP_OK) return s2;
+      if ((s2 = xmerged(0, true, 1, 0.0, 0.5)) != WP_OK || (s2 = zmerged(F_IFFT | F_PHASE)) != WP_OK) return s2;
     } else {
-      if ((s2 = zpass(F_FFT)) != WP_OK || (s2 = xpass(1)) != WP_OK) return s2;
-      for (int64_t k = 0; k < m; k++)
-        if ((s2 = prep(k == 0 ? 0 : 1, 0.5, 1.0)) != WP_OK || (s2 = zpass(F_IFFT | F_PHASE | F_FFT)) != WP_OK ||
-            (s2 = xpass(k == m - 1 ? 1 : 0)) != WP_OK)
-          return s2;
-      if ((s2 = prep(1, 0.0, 0.0)) != WP_OK || (s2 = zpass(F_IFFT)) != WP_OK) return s2;
+      if ((s2 = zmerged(F_FFT)) != WP_OK || (s2 = xmerged(1, true, 0, 0.5, 1.0)) != WP_OK) return s2;
+      for (int64_t k = 0; k < m; k++) {
+        if ((s2 = zmerged(F_IFFT | F_PHASE | F_FFT)) != WP_OK) return s2;
+        if (k < m - 1)
+          s2 = xmerged(0, true, 1, 0.5, 1.0);
+        else
+          s2 = xmerged(1, true, 1, 0.0, 0.0);
+        if (s2 != WP_OK) return s2;
+      }
+      if ((s2 = zmerged(F_IFFT)) != WP_OK) return s2;
     }
   }
   for (int k : b->idx_other) {
@@ -1470,6 +1597,10 @@ int wp_kernel_count(void) { return K_NCLASSES; }
 const char* wp_kernel_name(int k) { return (k >= 0 && k < K_NCLASSES) ? kClassNames[k] : ""; }
 
 wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
+  return wp_create_pooled(pb, stream, nullptr, out);
+}
+
+wp_status wp_create_pooled(const wp_problem* pb, void* stream, void* mem_pool, wp_handle** out) {
   if (!out) return fail(nullptr, WP_EINVAL, "out is NULL");
   *out = nullptr;
   wp_status st = validate_problem(pb);
@@ -1477,6 +1608,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
   wp_handle* h = new (std::nothrow) wp_handle();
   if (!h) return fail(nullptr, WP_ENOMEM, "host allocation failed");
   h->pb = *pb;
+  h->pool = (cudaMemPool_t)mem_pool;
   h->stream = (cudaStream_t)stream;
   h->graphs_on = stream != nullptr;
   h->ndim = pb->ndim;
@@ -1508,15 +1640,16 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     return s;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&h->state, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state allocation"));
+  if ((e = dev_malloc(h, &h->state, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "state allocation"));
   if ((e = cudaMemsetAsync(h->state, 0, bytes, h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
   if (h->ndim > 1)
-    if ((e = cudaMalloc(&h->scratch, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "scratch allocation"));
+    if ((e = dev_malloc(h, &h->scratch, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "scratch allocation"));
   if (pb->autocorr)
-    if ((e = cudaMalloc(&h->psi0, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "psi0 allocation"));
-  if ((e = cudaMalloc(&h->ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(cuda_fail(h, e, "ctrl allocation"));
+    if ((e = dev_malloc(h, &h->psi0, bytes)) != cudaSuccess) return bail(cuda_fail(h, e, "psi0 allocation"));
+  if ((e = dev_malloc(h, (void**)&h->ctrl, sizeof(Ctrl))) != cudaSuccess) return bail(cuda_fail(h, e, "ctrl allocation"));
   if ((e = cudaMemsetAsync(h->ctrl, 0, sizeof(Ctrl), h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "memset"));
-  if ((e = cudaMalloc(&h->dpot, sizeof(DevPot))) != cudaSuccess) return bail(cuda_fail(h, e, "potential allocation"));
+  if ((e = dev_malloc(h, (void**)&h->dpot, sizeof(DevPot))) != cudaSuccess)
+    return bail(cuda_fail(h, e, "potential allocation"));
   memset(&h->hpot, 0, sizeof(DevPot));
   if ((e = cudaMemcpyAsync(h->dpot, &h->hpot, sizeof(DevPot), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, e, "potential copy"));
@@ -1526,10 +1659,10 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     const size_t rec = h->prec == WP_C64 ? sizeof(LineRec<float>) : sizeof(LineRec<double>);
     h->nlines_phase = h->N / h->n[h->ndim - 1];
     h->nlines_kin = h->N / h->n[0];
-    if ((e = cudaMalloc(&h->lines_phase, rec * h->nlines_phase)) != cudaSuccess)
+    if ((e = dev_malloc(h, &h->lines_phase, rec * h->nlines_phase)) != cudaSuccess)
       return bail(cuda_fail(h, e, "line-record allocation"));
     for (int k = 0; k < 2; k++)
-      if ((e = cudaMalloc(&h->lines_kin[k], rec * h->nlines_kin)) != cudaSuccess)
+      if ((e = dev_malloc(h, &h->lines_kin[k], rec * h->nlines_kin)) != cudaSuccess)
         return bail(cuda_fail(h, e, "line-record allocation"));
     for (int k = 0; k < 2; k++)
       if ((st = WP_DISPATCH(h, run_lines<T>(h, false, k))) != WP_OK) return bail(st);
@@ -1543,7 +1676,7 @@ wp_status wp_create(const wp_problem* pb, void* stream, wp_handle** out) {
     if (tune_cache_get(h, &cached)) apply_schedule(h, cached);
   }
   if (h->ndim == 1) {
-    if ((e = cudaMalloc(&h->res_S, 2 * (size_t)h->n[0] * sizeof(TwE<double>))) != cudaSuccess)
+    if ((e = dev_malloc(h, &h->res_S, 2 * (size_t)h->n[0] * sizeof(TwE<double>))) != cudaSuccess)
       return bail(cuda_fail(h, e, "static phase allocation"));
     if ((st = res1d_split_potential(h)) != WP_OK) return bail(st);
   }
@@ -1560,8 +1693,8 @@ wp_status wp_destroy(wp_handle* h) {
   void* ptrs[] = {h->state,    h->scratch,  h->psi0,     h->staging,     h->ctrl,          h->dpot,
                   h->tabmem,   h->part_pos, h->part_mom, h->obs_dev,     h->lines_phase,   h->lines_kin[0],
                   h->lines_kin[1], h->res_S, h->gauss_tab, h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) dev_free(h, p);
+  if (h->pool) cudaStreamSynchronize(h->stream);
   for (auto& ep : h->pending) {
     cudaEventDestroy(ep.a);
     cudaEventDestroy(ep.b);
@@ -1611,18 +1744,17 @@ wp_status wp_set_potential_grid(wp_handle* h, const double* V, int on_device) {
   WP_CUDA(h, cudaStreamSynchronize(h->stream));
   graphs_clear(h);
   if (!V) {
-    for (void* q : {(void*)h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]})
-      if (q) cudaFree(q);
+    for (void* q : {(void*)h->vgrid, h->vgrid_rec[0], h->vgrid_rec[1]}) dev_free(h, q);
     h->vgrid = nullptr;
     h->vgrid_rec[0] = h->vgrid_rec[1] = nullptr;
   } else {
     const size_t bytes = (size_t)h->N * sizeof(double);
-    if (!h->vgrid) WP_CUDA(h, cudaMalloc(&h->vgrid, bytes));
+    if (!h->vgrid) WP_CUDA(h, dev_malloc(h, (void**)&h->vgrid, bytes));
     WP_CUDA(h, cudaMemcpyAsync(h->vgrid, V, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                h->stream));
     if (h->ndim > 1) {
       for (int k = 0; k < 2; k++)
-        if (!h->vgrid_rec[k]) WP_CUDA(h, cudaMalloc(&h->vgrid_rec[k], (size_t)h->N * sizeof(TwE<double>)));
+        if (!h->vgrid_rec[k]) WP_CUDA(h, dev_malloc(h, &h->vgrid_rec[k], (size_t)h->N * sizeof(TwE<double>)));
       const wp_status st = WP_DISPATCH(h, grid_phase_tables<T>(h));
       if (st != WP_OK) return st;
     }
@@ -1638,7 +1770,7 @@ wp_status wp_expect_grid(wp_handle* h, const double* A, int on_device, double* o
   const int64_t nb = (h->N + per_block - 1) / per_block;
   const size_t abytes = on_device ? 0 : (size_t)h->N * sizeof(double);
   char* tmp = nullptr;
-  WP_CUDA(h, cudaMalloc(&tmp, abytes + (size_t)(nb + 1) * sizeof(double)));
+  WP_CUDA(h, dev_malloc(h, (void**)&tmp, abytes + (size_t)(nb + 1) * sizeof(double)));
   const double* Ad = A;
   cudaError_t e = cudaSuccess;
   if (!on_device) {
@@ -1666,7 +1798,7 @@ wp_status wp_expect_grid(wp_handle* h, const double* A, int on_device, double* o
     if (e != cudaSuccess) st = cuda_fail(h, e, "expectation result");
   }
   cudaStreamSynchronize(h->stream);
-  cudaFree(tmp);
+  dev_free(h, tmp);
   return st;
 }
 
@@ -1704,7 +1836,7 @@ wp_status wp_set_state(wp_handle* h, const void* psi, int on_device) {
   } else {
     const void* src = psi;
     if (!on_device) {
-      if (!h->staging) WP_CUDA(h, cudaMalloc(&h->staging, bytes128));
+      if (!h->staging) WP_CUDA(h, dev_malloc(h, &h->staging, bytes128));
       WP_CUDA(h, cudaMemcpyAsync(h->staging, psi, bytes128, cudaMemcpyHostToDevice, h->stream));
       src = h->staging;
     }
@@ -1723,7 +1855,7 @@ wp_status wp_get_state(wp_handle* h, void* dst, int on_device) {
   } else {
     void* tgt = dst;
     if (!on_device) {
-      if (!h->staging) WP_CUDA(h, cudaMalloc(&h->staging, bytes128));
+      if (!h->staging) WP_CUDA(h, dev_malloc(h, &h->staging, bytes128));
       tgt = h->staging;
     }
     wp_status st = WP_DISPATCH(h, convert_out<T>(h, tgt));
@@ -1832,7 +1964,7 @@ wp_status wp_autotune(wp_handle* h, int32_t steps, wp_schedule* best, double* be
   const int64_t step0 = h->host_step;
   const size_t bytes = (size_t)h->N * h->elem;
   void* save = nullptr;
-  cudaError_t e = cudaMalloc(&save, bytes);
+  cudaError_t e = dev_malloc(h, &save, bytes);
   if (e != cudaSuccess) return cuda_fail(h, e, "autotune state copy");
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   wp_status st = WP_OK;
@@ -1889,7 +2021,7 @@ wp_status wp_autotune(wp_handle* h, int32_t steps, wp_schedule* best, double* be
   cudaStreamSynchronize(h->stream);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
-  cudaFree(save);
+  dev_free(h, save);
   if (st != WP_OK) return st;
   if (best) *best = win;
   if (best_ms) *best_ms = win_ms;

@@ -154,7 +154,8 @@ struct AxisTab {
   cx<T>* Ox;                  // (x_i, x_i^2) in T: line sums of the position moments
   cx<T>* Ok;                  // (k_i, k_i^2) in T: line sums of the momentum moments
   T* AT;                      // A(x,t) rounded to T: line sums of the potential energy
-  void* W256;                 // complex64, n = 256: records exp(-2 pi i t k1/256) at k1 * 16 + t
+  void* W256;                 // complex64 and float-float, n = 256: records exp(-2 pi i t k1/256) at k1 * 16 + t
+  void* W2s;                  // complex64, n = 64 or 128: two-stage twiddle records (wp_pass2s.cuh)
 };
 
 template <class T>
@@ -202,6 +203,7 @@ struct PassParams {
   const TwE<T>* grid_rec;  // static grid potential: phase records of this pass's tau, or NULL
   const double* grid_v;    // static grid potential (observables), or NULL
   const void* W256;        // two-stage 256-point kernels: twiddle records of the pass axis, or NULL
+  const void* W2s;         // two-stage 64- and 128-point kernels: twiddle records, or NULL
 };
 
 // Per-line records of one pass (k_lines).
@@ -356,16 +358,51 @@ int launch_add_step(Ctrl* ctrl, int64_t add, void* stream);
 template <class T> int pass_smem_limit_set(size_t smem);
 // fixed-size pass kernels (their own translation units, wp_fixed_*.cu)
 template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
-// two-stage complex64 kernels for 256-point lines (wp_pass256_f32.cu)
-bool pass256_applies(const PassParams<float>& p);
-int launch_pass256(const PassParams<float>& p, void* stream);
+// One launch per batched pass (wp_batch_merged.cuh): class c of the pass covers launch
+// blocks start[c] .. start[c + 1] - 1 and block-list entries list_off[c] on; key[c] is its
+// line-length class (6..10 fixed-shape, kBatchClassP256 + v two-stage). nprep trailing
+// blocks form the per-instance tables (and, with lines, the line records) of the next
+// step, with the step increment, time shift and phase length (units of dt) given.
+constexpr int kMergedMaxClasses = 8;
+struct MergedLaunch {
+  int32_t ncls;
+  int32_t key[kMergedMaxClasses];
+  int64_t start[kMergedMaxClasses + 1];
+  int64_t list_off[kMergedMaxClasses];
+  int32_t nprep;
+  int32_t step_add;
+  double shift_dt, tau_dt;
+  int32_t lines;
+};
+template <class T>
+int launch_merged_contig(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst,
+                         const MergedLaunch& ml, uint32_t flags, int khalf, const PrepParams<T>* pp,
+                         const LinesParams<T>* lp, size_t smem, void* stream);
+template <class T>
+int launch_merged_strided(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst,
+                          const MergedLaunch& ml, uint32_t flags, int khalf, const PrepParams<T>* pp,
+                          const LinesParams<T>* lp, size_t smem, void* stream);
+
+// two-stage kernels for 256-point lines, complex64 and float-float (wp_pass256_*.cu)
+template <class T> bool pass256_applies(const PassParams<T>& p);
+template <class T> int launch_pass256(const PassParams<T>& p, void* stream);
+// complex64 two-stage kernels for 64- and 128-point lines (wp_pass2s_f32.cu), single and
+// batched (class keys kBatchClassP2S + 100 (logn - 6) + v, v as for the 256-point class)
+constexpr int kBatchClassP2S = 1100;
+constexpr size_t kPass2sSmem = 136 * 16 + 16 * 137 * 8;  // the larger of their two shared-memory sizes
+bool pass2s_applies(const PassParams<float>& p);
+int launch_pass2s(const PassParams<float>& p, void* stream);
+int launch_pass2s_batch(const PassParams<float>* params, const int64_t* tile_start, const int* block_inst, int logn,
+                        int variant, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
 // their batched form: one launch over a class of blocks (16-line or 16-column tiles).
 // Class keys kBatchClassP256 + v in a batch's block lists, v = 2 x (largest Gaussian-term
 // count) + (any additive terms) for the contiguous pass, 0 for the strided one; variant
 // -1 selects the strided FFT-only kernel.
 constexpr int kBatchClassP256 = 1000;
-int launch_pass256_batch(const PassParams<float>* params, const int64_t* tile_start, const int* block_inst,
-                         int variant, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
+constexpr size_t kPass256Smem = 256 * 16 + 16 * 273 * 8;  // their dynamic shared memory
+template <class T>
+int launch_pass256_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int variant,
+                         int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream);
 template <class T> int fixed_smem_limit_set(size_t smem);
 // batched pass kernels, contiguous and strided axis (wp_batch_*.cu): one launch per
 // line-length class, blocks block_off .. block_off + nblocks - 1 of the class-sorted list

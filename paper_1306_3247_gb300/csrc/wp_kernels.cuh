@@ -1164,15 +1164,15 @@ __global__ void __launch_bounds__(32 * E) k_pass(const PassParams<T> p) {
 // tiles its lines into 2048-element tiles with 256 threads. The block copies its
 // instance's parameters to shared memory and runs the pass body: LOGN = 6..10 the
 // compile-time-shape body (with per-line records), LOGN = 0 the run-time one.
+// raw: a 16-byte aligned shared-memory buffer of sizeof(PassParams<T>) bytes for the
+// instance's parameters (the caller's, so that several bodies in one kernel share it).
 template <class T, bool CONTIG, int LOGN>
 __device__ __forceinline__ void pass_batch_body(const PassParams<T>* __restrict__ params,
                                                 const int64_t* __restrict__ tile_start,
-                                                const int* __restrict__ block_inst, int64_t block_off, uint32_t flags,
-                                                int khalf) {
+                                                const int* __restrict__ block_inst, int64_t blk, uint32_t flags,
+                                                int khalf, unsigned char* raw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
   PassParams<T>& p = *reinterpret_cast<PassParams<T>*>(raw);
-  const int64_t blk = block_off + blockIdx.x;
   const int inst = block_inst[blk];
   const int64_t tile = blk - tile_start[inst];
   // fixed shapes: the tile loads need only the state pointer and the axis stride, so they
@@ -1243,7 +1243,8 @@ __global__ void __launch_bounds__(256) k_pass_batch(const PassParams<T>* __restr
                                                     const int64_t* __restrict__ tile_start,
                                                     const int* __restrict__ block_inst, int64_t block_off,
                                                     uint32_t flags, int khalf) {
-  pass_batch_body<T, CONTIG, LOGN>(params, tile_start, block_inst, block_off, flags, khalf);
+  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
+  pass_batch_body<T, CONTIG, LOGN>(params, tile_start, block_inst, block_off + blockIdx.x, flags, khalf, raw);
 }
 // FP64 with a compile-time shape (LOGN = 6..10): at most 64 registers, so that four
 // blocks share an SM (the FP64 pipe needs the warps to cover its latency).
@@ -1252,11 +1253,12 @@ __global__ void __launch_bounds__(256, 4) k_pass_batch_f64(const PassParams<doub
                                                           const int64_t* __restrict__ tile_start,
                                                           const int* __restrict__ block_inst, int64_t block_off,
                                                           uint32_t flags, int khalf) {
-  pass_batch_body<double, CONTIG, LOGN>(params, tile_start, block_inst, block_off, flags, khalf);
+  __shared__ __align__(16) unsigned char raw[sizeof(PassParams<double>)];
+  pass_batch_body<double, CONTIG, LOGN>(params, tile_start, block_inst, block_off + blockIdx.x, flags, khalf, raw);
 }
 
 template <class T>
-__device__ void lines_body(const LinesParams<T>& p);
+__device__ void lines_body(const LinesParams<T>& p, int64_t first, int64_t stride);
 
 // Batched per-line records: blockIdx.y selects the instance, x strides over its lines.
 template <class T>
@@ -1267,7 +1269,7 @@ __global__ void __launch_bounds__(256) k_lines_batch(const LinesParams<T>* __res
     reinterpret_cast<int*>(raw)[k] = src[k];
   __syncthreads();
   const LinesParams<T>& p = *reinterpret_cast<const LinesParams<T>*>(raw);
-  lines_body<T>(p);
+  lines_body<T>(p, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Fixed-size pass: n = 2^LOGN points per line, 2048-element tiles, 256 threads.
@@ -1290,12 +1292,11 @@ __global__ void __launch_bounds__(256, (OBS || GRID) ? 3 : 4) k_pass_fixed_f64(c
 // ------------------------------------------------------------------ per-line records
 // One record per line of a pass: the FP64 product of the other axes' factors (high +
 // low table parts), rounded to a record, and the per-line Gaussian-term phase
-// coefficients. Grid-stride over the lines.
+// coefficients. Lines first, first + stride, ...
 template <class T>
-__device__ void lines_body(const LinesParams<T>& p) {
+__device__ void lines_body(const LinesParams<T>& p, int64_t first, int64_t stride) {
   const bool contig = (p.axis == p.g.ndim - 1);
-  for (int64_t line = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; line < p.nlines;
-       line += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t line = first; line < p.nlines; line += stride) {
     int gi[3];
     if (contig)
       grid_index(p.g, p.axis, line, 0, 0, gi);
@@ -1327,7 +1328,7 @@ __device__ void lines_body(const LinesParams<T>& p) {
 
 template <class T>
 __global__ void __launch_bounds__(256) k_lines(const LinesParams<T> p) {
-  lines_body<T>(p);
+  lines_body<T>(p, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------------ per-step tables

@@ -44,8 +44,11 @@ int launch_pass(const PassParams<T>& p, int64_t ntiles, size_t smem, void* strea
   const bool obs = (p.flags & (F_OBS_POS | F_OBS_MOM)) != 0;
   const dim3 grid((unsigned)ntiles), block(p.nthreads);
   cudaStream_t st = (cudaStream_t)stream;
+  if constexpr (!std::is_same<T, double>::value) {
+    if (pass256_applies<T>(p)) return launch_pass256<T>(p, stream);
+  }
   if constexpr (std::is_same<T, float>::value) {
-    if (pass256_applies(p)) return launch_pass256(p, stream);
+    if (pass2s_applies(p)) return launch_pass2s(p, stream);
   }
   if (p.fixed) {
     if (p.nthreads != 256 || p.logC != 11 - p.logn) return (int)cudaErrorInvalidConfiguration;
@@ -160,9 +163,14 @@ int launch_pass_batch(const PassParams<T>* params, const int64_t* tile_start, co
                       int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, size_t smem, void* stream) {
   // the two-stage complex64 kernels of 256-point lines have a class of their own
   if constexpr (std::is_same<T, float>::value) {
+    if (logn >= kBatchClassP2S && logn < kBatchClassP2S + 200)
+      return launch_pass2s_batch(params, tile_start, block_inst, 6 + (logn - kBatchClassP2S) / 100,
+                                 (logn - kBatchClassP2S) % 100, block_off, nblocks, flags, khalf, stream);
+  }
+  if constexpr (!std::is_same<T, double>::value) {
     if (logn >= kBatchClassP256 && logn < kBatchClassP256 + 6)
-      return launch_pass256_batch(params, tile_start, block_inst, logn - kBatchClassP256, block_off, nblocks, flags,
-                                  khalf, stream);
+      return launch_pass256_batch<T>(params, tile_start, block_inst, logn - kBatchClassP256, block_off, nblocks,
+                                     flags, khalf, stream);
   }
   // the contiguous pass carries the potential phase, the strided one the kinetic factor
   if ((flags & F_KIN) == 0)

@@ -1,0 +1,121 @@
+// Host launchers of the two-stage 256-point pass kernels (wp_pass256.cuh), shared by the
+// translation units of the complex64 and float-float forms.
+#pragma once
+
+#include <type_traits>
+
+#include "wp_pass256.cuh"
+
+namespace wp {
+namespace p256_detail {
+
+template <class T>
+constexpr bool two_stage_strided() { return std::is_same<T, float>::value; }
+
+// The two-stage kernels serve a pass when: 256 points along the axis, the fixed-shape
+// schedule, no partial sums, no grid potential, and whole tiles (L lines of a contiguous
+// axis, L adjacent columns of a strided one; L = 16 complex64, 8 float-float).
+template <class T>
+bool applies(const PassParams<T>& p) {
+  if (!p.fixed || p.logn != p256::kLogN || !p.W256) return false;
+  if (p.flags & (F_OBS_POS | F_OBS_MOM | F_NO_STORE | F_AUTOCORR)) return false;
+  if (p.grid_rec && (p.flags & F_PHASE)) return false;
+  int lntot = 0;
+  for (int d = 0; d < p.g.ndim; d++) lntot += p.g.ln[d];
+  const int lines_log = lntot - p256::kLogN;
+  constexpr int LL = p256::Shape<T>::kLogLines;
+  if (p.log_inner == 0) return lines_log >= LL && !(p.flags & F_KIN);
+  if (p.flags & F_PHASE) return false;  // the potential phase runs on the contiguous axis
+  // float-float: measured on the 256^3 job, its two-stage strided passes were slower than
+  // the Stockham ones (180 against 155 us FFT-only, 403 against 324 us kinetic: its
+  // arithmetic dominates, so the two-stage form saves only 5 % of the instructions, and at
+  // 128 registers it runs 16 warps per SM), while its contiguous pass is faster (336
+  // against 391 us): float-float takes the two-stage kernels on the contiguous axis only
+  if (!two_stage_strided<T>()) return false;
+  return p.log_inner >= LL;
+}
+
+// The contiguous kernel of the potential's kind: Gaussian terms (0..2), additive terms.
+template <class T, int NG>
+void launch_contig_ng(const PassParams<T>& p, unsigned blocks, cudaStream_t st) {
+  if (p.sep)
+    p256::k_pass256_contig<T, NG, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+  else
+    p256::k_pass256_contig<T, NG, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+}
+
+template <class T>
+int launch(const PassParams<T>& p, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int lntot = 0;
+  for (int d = 0; d < p.g.ndim; d++) lntot += p.g.ln[d];
+  const unsigned blocks = (unsigned)(int64_t(1) << (lntot - p256::kLogN - p256::Shape<T>::kLogLines));
+  if (p.log_inner == 0) {
+    const int ng = (p.flags & F_PHASE) ? p.ngauss : 0;
+    PassParams<T> q = p;
+    q.sep = ((p.flags & F_PHASE) && p.sep) ? 1 : 0;
+    if (ng >= 2)
+      launch_contig_ng<T, 2>(q, blocks, st);
+    else if (ng == 1)
+      launch_contig_ng<T, 1>(q, blocks, st);
+    else
+      launch_contig_ng<T, 0>(q, blocks, st);
+  } else if (p.flags & F_KIN) {
+    p256::k_pass256_strided<T, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+  } else {
+    p256::k_pass256_strided<T, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+template <class T>
+int launch_batch(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst, int variant,
+                 int64_t block_off, int64_t nblocks, uint32_t flags, int khalf, void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (nblocks > 0) {
+    const dim3 grid((unsigned)nblocks), block(p256::threads_of<T>());
+    auto go = [&](auto kern) { kern<<<grid, block, p256::kSmem, st>>>(params, tile_start, block_inst, block_off, flags,
+                                                                      khalf); };
+    if (flags & F_KIN) {
+      go(p256::k_pass256_batch<T, false, true>);
+    } else if (variant < 0) {
+      go(p256::k_pass256_batch<T, false, false>);
+    } else {
+      // contiguous: the class's largest Gaussian-term count and whether any instance has
+      // additive terms (an instance without them multiplies by factors that are exactly 1)
+      const int ng = (flags & F_PHASE) ? variant >> 1 : 0;
+      const bool sep = (flags & F_PHASE) && (variant & 1);
+      if (ng == 0)
+        sep ? go(p256::k_pass256_batch<T, true, false, 0, true>) : go(p256::k_pass256_batch<T, true, false, 0, false>);
+      else if (ng == 1)
+        sep ? go(p256::k_pass256_batch<T, true, false, 1, true>) : go(p256::k_pass256_batch<T, true, false, 1, false>);
+      else
+        sep ? go(p256::k_pass256_batch<T, true, false, 2, true>) : go(p256::k_pass256_batch<T, true, false, 2, false>);
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+}  // namespace p256_detail
+}  // namespace wp
+
+#define WP_PASS256_TU(T)                                                                                       \
+  namespace wp {                                                                                               \
+  template <>                                                                                                  \
+  bool pass256_applies<T>(const PassParams<T>& p) {                                                            \
+    return p256_detail::applies<T>(p);                                                                         \
+  }                                                                                                            \
+  template <>                                                                                                  \
+  int launch_pass256<T>(const PassParams<T>& p, void* stream) {                                                \
+    return p256_detail::launch<T>(p, stream);                                                                  \
+  }                                                                                                            \
+  template <>                                                                                                  \
+  int launch_pass256_batch<T>(const PassParams<T>* params, const int64_t* tile_start, const int* block_inst,   \
+                              int variant, int64_t block_off, int64_t nblocks, uint32_t flags, int khalf,      \
+                              void* stream) {                                                                  \
+    return p256_detail::launch_batch<T>(params, tile_start, block_inst, variant, block_off, nblocks, flags,    \
+                                        khalf, stream);                                                        \
+  }                                                                                                            \
+  }

@@ -6,6 +6,12 @@
 // finished. Each running request owns one stream of the pool, so the kernels of
 // different requests overlap on the device; a request's arithmetic is exactly that of
 // its handle alone (the result does not depend on the mix).
+//
+// Device memory: wp_server_create reserves the budget in a CUDA memory pool (its release
+// threshold keeps the memory after frees), and every admitted request's handle takes its
+// buffers from that pool with stream-ordered allocations (wp_create_pooled), so admission
+// and completion call neither cudaMalloc nor cudaFree. Should the pool be too fragmented
+// to serve an admission, the request waits in the queue for the next progress call.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -62,6 +68,7 @@ int64_t job_bytes(const wp_problem& pb) {
 struct wp_server {
   int64_t budget = 0, in_use = 0;
   int64_t chunk = 50;
+  cudaMemPool_t pool = nullptr;
   std::vector<cudaStream_t> streams;
   std::vector<cudaEvent_t> events;
   std::vector<int64_t> slot_job;  // job id on the slot, -1 when free
@@ -89,7 +96,7 @@ wp_status issue_chunk(wp_server* s, Job& j) {
 
 wp_status admit(wp_server* s, Job& j, int slot) {
   wp_problem pb = j.pb;
-  wp_status st = wp_create(&pb, s->streams[slot], &j.h);
+  wp_status st = wp_create_pooled(&pb, s->streams[slot], s->pool, &j.h);
   if (st != WP_OK) return sfail(s, st, wp_last_error(nullptr));
   if ((st = wp_set_potential(j.h, &j.pot)) != WP_OK || (st = wp_init_gaussian(j.h, j.x0, j.p0, j.sigma)) != WP_OK) {
     s->err = wp_last_error(j.h);
@@ -116,6 +123,29 @@ wp_status wp_server_create(int64_t budget_bytes, int32_t nslots, int64_t chunk_s
   if (!s) return WP_ENOMEM;
   s->budget = budget_bytes;
   s->chunk = chunk_steps;
+  {
+    // the pool of the current device, holding on to up to the budget once reserved
+    int dev = 0;
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    cudaError_t e = cudaGetDevice(&dev);
+    props.location.id = dev;
+    if (e == cudaSuccess) e = cudaMemPoolCreate(&s->pool, &props);
+    uint64_t keep = (uint64_t)budget_bytes;
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    // reserve: one allocation of the whole budget, returned to the pool at once
+    void* p = nullptr;
+    if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&p, (size_t)budget_bytes, s->pool, (cudaStream_t)0);
+    if (e == cudaSuccess) e = cudaFreeAsync(p, (cudaStream_t)0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)0);
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      if (s->pool) cudaMemPoolDestroy(s->pool);
+      delete s;
+      return e == cudaErrorMemoryAllocation ? WP_ENOMEM : WP_ECUDA;
+    }
+  }
   for (int k = 0; k < nslots; k++) {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
@@ -124,6 +154,7 @@ wp_status wp_server_create(int64_t budget_bytes, int32_t nslots, int64_t chunk_s
       for (auto x : s->streams) cudaStreamDestroy(x);
       for (auto x : s->events) cudaEventDestroy(x);
       if (st) cudaStreamDestroy(st);
+      cudaMemPoolDestroy(s->pool);
       delete s;
       return WP_ECUDA;
     }
@@ -192,6 +223,13 @@ wp_status wp_server_progress(wp_server* s, int64_t* done_ids, int64_t cap, int64
     if (slot < 0) break;
     s->queue.pop_front();
     wp_status st = admit(s, j, slot);
+    if (st == WP_ENOMEM && j.h == nullptr && s->in_use > 0) {
+      // the pool could not serve the buffers now: the request waits for running ones to
+      // finish and free theirs (the budget was checked above)
+      (void)cudaGetLastError();
+      s->queue.push_front(j.id);
+      break;
+    }
     if (st != WP_OK) {
       // the request cannot run (e.g. an unsupported grid): finish it with its error
       if (j.h) {
@@ -265,6 +303,7 @@ wp_status wp_server_destroy(wp_server* s) {
     cudaStreamDestroy(st);
   }
   for (auto ev : s->events) cudaEventDestroy(ev);
+  if (s->pool) cudaMemPoolDestroy(s->pool);
   delete s;
   return WP_OK;
 }

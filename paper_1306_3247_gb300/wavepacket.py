@@ -94,6 +94,7 @@ def load_library(build_if_missing: bool = True):
     H = vp
     sig = {
         "wp_create": ([P(WpProblem), vp, P(vp)], ctypes.c_int),
+        "wp_create_pooled": ([P(WpProblem), vp, vp, P(vp)], ctypes.c_int),
         "wp_set_potential": ([H, P(WpPotential)], ctypes.c_int),
         "wp_set_state": ([H, vp, ctypes.c_int], ctypes.c_int),
         "wp_init_gaussian": ([H, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)], ctypes.c_int),
@@ -202,10 +203,15 @@ def make_potential(terms) -> WpPotential:
 
 
 # ---------------------------------------------------------------- C ABI names
-def wp_create(problem: WpProblem, stream=None):
+def wp_create(problem: WpProblem, stream=None, mem_pool=None):
+    """mem_pool: a cudaMemPool_t (int address) to take the handle's device memory from."""
     lib = load_library()
     h = ctypes.c_void_p()
-    st = lib.wp_create(ctypes.byref(problem), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+    if mem_pool:
+        st = lib.wp_create_pooled(ctypes.byref(problem), ctypes.c_void_p(stream or 0), ctypes.c_void_p(mem_pool),
+                                  ctypes.byref(h))
+    else:
+        st = lib.wp_create(ctypes.byref(problem), ctypes.c_void_p(stream or 0), ctypes.byref(h))
     _check(lib, None, st)
     return h
 
@@ -398,12 +404,12 @@ def _current_stream():
 class Propagator:
     """One propagation on the GPU. problem/terms use the workloads.py schema."""
 
-    def __init__(self, problem: dict, terms=(), precision="c128", autocorr=False, stream=None):
+    def __init__(self, problem: dict, terms=(), precision="c128", autocorr=False, stream=None, mem_pool=None):
         self.problem = dict(problem)
         self.precision = precision
         self.shape = tuple(int(x) for x in problem["n"][: int(problem["ndim"])])
         self._pb = make_problem(problem, precision, autocorr)
-        self.h = wp_create(self._pb, stream)
+        self.h = wp_create(self._pb, stream, mem_pool)
         if terms:
             self.set_potential(terms)
 

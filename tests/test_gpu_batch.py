@@ -78,3 +78,19 @@ def test_batch_kvk_and_mixed_dims():
         pb, terms = cfg["problem"], cfg["terms"]
         ref = O.propagate(pb, terms, O.gaussian(pb, **cfg["init"]), 18)
         assert rel_l2(got[k], ref) < 1e-11, (k, pb["n"])
+
+
+def test_batch_matches_oracle_c64():
+    # the complex64 batch (two-stage kernels for 64-, 128- and 256-point axes, Stockham
+    # for the rest) against the oracle, within the form's 2e-4
+    mix = small_mix(count=12, seed=13)
+    with WPK.Batch("c64") as B:
+        for cfg in mix:
+            k = B.add(cfg["problem"], cfg["terms"])
+            B.init_gaussian(k, **cfg["init"])
+        B.step(40)
+        got = [B.get_state(k) for k in range(len(mix))]
+    for k, cfg in enumerate(mix):
+        pb, terms = cfg["problem"], cfg["terms"]
+        ref = O.propagate(pb, terms, O.gaussian(pb, **cfg["init"]), 40)
+        assert rel_l2(got[k], ref) < 2e-4, (k, pb["n"])

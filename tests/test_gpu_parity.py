@@ -56,22 +56,81 @@ def test_fft_matches_oracle(shape, prec):
         assert rel_l2(P.get_state() / x.size, x) < tol
 
 
-# Shapes that run the two-stage complex64 kernels for 256-point lines: the contiguous axis
-# with 16, 32 or 64 lines, and strided axes with 16 or more adjacent columns (the kernels
-# run in complex64 only; complex128 runs the same shapes on the Stockham kernels).
-@pytest.mark.parametrize("shape", [(16, 256), (256, 16), (256, 256), (4, 256, 32), (256, 2, 16), (2, 256, 64)])
-@pytest.mark.parametrize("prec", ["c64", "c128"])
+# Shapes that run the two-stage kernels for 256-point lines: the contiguous axis with 8
+# (float-float) or 16 (complex64) lines or more, and strided axes with as many adjacent
+# columns; smaller ones keep the Stockham kernels. Native complex128 runs every shape on
+# the Stockham kernels.
+@pytest.mark.parametrize("shape", [(16, 256), (256, 16), (256, 256), (4, 256, 32), (256, 2, 16), (2, 256, 64),
+                                   (8, 256), (256, 8), (256, 4, 2)])
+@pytest.mark.parametrize("prec", ["c64", "c128f", "c128"])
 def test_fft_256_lines_match_oracle(shape, prec):
     nd = len(shape)
     pb = {"ndim": nd, "n": list(shape), "xmin": [0.0] * nd, "L": [1.0] * nd, "dt": 0.1}
     x = W.random_state(shape, seed=7 * sum(shape))
-    tol = {"c128": 1e-13, "c64": 3e-6}[prec]
+    tol = {"c128": 1e-13, "c64": 3e-6, "c128f": 1e-12}[prec]
     with WPK.Propagator(pb, precision=prec) as P:
         P.set_state(x)
         P.fft(-1)
         assert rel_l2(P.get_state(), O.fft(x, -1)) < tol
         P.fft(+1)
         assert rel_l2(P.get_state() / x.size, x) < tol
+
+
+# Shapes that run the two-stage complex64 kernels for 64- and 128-point lines (32 lines or
+# columns per tile for 64, 16 for 128), and smaller ones that keep the Stockham kernels.
+@pytest.mark.parametrize("shape", [(32, 64), (64, 32), (16, 128), (128, 16), (64, 64), (128, 128), (64, 128),
+                                   (2, 64, 32), (32, 2, 64), (4, 128, 16), (16, 64), (64, 16)])
+def test_fft_64_128_lines_match_oracle_c64(shape):
+    nd = len(shape)
+    pb = {"ndim": nd, "n": list(shape), "xmin": [0.0] * nd, "L": [1.0] * nd, "dt": 0.1}
+    x = W.random_state(shape, seed=11 * sum(shape))
+    with WPK.Propagator(pb, precision="c64") as P:
+        P.set_state(x)
+        P.fft(-1)
+        assert rel_l2(P.get_state(), O.fft(x, -1)) < 3e-6
+        P.fft(+1)
+        assert rel_l2(P.get_state() / x.size, x) < 3e-6
+
+
+@pytest.mark.parametrize("shape", [(64, 64), (128, 64), (64, 128)])
+def test_2d_64_128_c64_1000_steps(shape):
+    # 64- and 128-point axes on the two-stage complex64 kernels: driven trap plus barrier
+    pb = {"ndim": 2, "n": list(shape), "xmin": [-12.0, -10.0], "L": [24.0, 20.0], "mass": 1.0, "hbar": 1.0,
+          "dt": 0.005, "t0": 0.0}
+    terms = [{"shape": "quad", "a": [0.5, 0.8], "coef": {"A0": 1.0}},
+             {"shape": "gauss", "a": [1.0, 1.2], "c0": [1.0, 0.0], "coef": {"A0": 1.0, "A": 0.3, "omega": 2.0}},
+             {"shape": "linear", "a": [1.0, 0.0], "coef": {"A": 0.1, "omega": 0.7}}]
+    psi0 = O.gaussian(pb, [-2.0, 0.5], [1.0, 0.0], [1.2, 1.0])
+    ref, ref_obs = O.run(pb, terms, psi0, 1000, 100)
+    with WPK.Propagator(pb, terms, "c64", autocorr=True) as P:
+        P.set_state(psi0)
+        obs = P.run(1000, 100)
+        psi = P.get_state()
+    err = rel_l2(psi, ref)
+    drift = float(np.max(np.abs(obs["norm"] - obs["norm"][0])))
+    print("c64", shape, "rel L2", err, "norm drift", drift)
+    assert err < TOL64
+    assert drift < 1e-5
+    compare_obs(obs, ref_obs, TOL64)
+
+
+def test_2d_256_square_c128f_1000_steps():
+    # 256^2 on the two-stage float-float kernels, at the complex128 bar
+    pb = {"ndim": 2, "n": [256, 256], "xmin": [-16.0, -16.0], "L": [32.0, 32.0], "mass": 1.0, "hbar": 1.0,
+          "dt": 0.005, "t0": 0.0}
+    terms = [{"shape": "quad", "a": [0.25, 0.5], "coef": {"A0": 1.0}},
+             {"shape": "gauss", "a": [1.0, 1.5], "c0": [1.0, 0.0], "coef": {"A0": 1.0, "A": 0.3, "omega": 2.0}},
+             {"shape": "linear", "a": [1.0, 0.0], "coef": {"A": 0.1, "omega": 0.7}}]
+    psi0 = O.gaussian(pb, [-2.0, 0.5], [1.5, 0.0], [1.2, 1.0])
+    ref, ref_obs = O.run(pb, terms, psi0, 1000, 100)
+    with WPK.Propagator(pb, terms, "c128f", autocorr=True) as P:
+        P.set_state(psi0)
+        obs = P.run(1000, 100)
+        psi = P.get_state()
+    err = rel_l2(psi, ref)
+    print("c128f 256^2 rel L2", err)
+    assert err < TOL128
+    compare_obs(obs, ref_obs, 1e-10)
 
 
 def test_2d_256_square_c64_1000_steps():

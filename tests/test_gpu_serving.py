@@ -1,5 +1,9 @@
 """Continuous-batching server: every request's result is the same alone and in the mix,
 admission respects the memory budget, and the latency bookkeeping is consistent."""
+import ctypes
+import ctypes.util
+import os
+
 import numpy as np
 import pytest
 
@@ -56,3 +60,54 @@ def test_budget_limits_concurrency():
         with pytest.raises(WPK.WavepacketError) as e:
             srv.submit(0, big["problem"], big["terms"], big["init"], 10)
         assert e.value.status == WPK.WP_ENOMEM
+
+
+def _cudart():
+    for cand in ("/usr/local/cuda/lib64/libcudart.so", ctypes.util.find_library("cudart")):
+        if cand and (os.path.sep not in cand or os.path.exists(cand)):
+            try:
+                return ctypes.CDLL(cand)
+            except OSError:
+                continue
+    pytest.skip("no CUDA runtime library to create a memory pool with")
+
+
+class _PoolProps(ctypes.Structure):
+    # cudaMemPoolProps: allocType, handleTypes, location {type, id}, win32 attributes,
+    # maxSize, usage, reserved bytes
+    _fields_ = [("allocType", ctypes.c_int), ("handleTypes", ctypes.c_int), ("loc_type", ctypes.c_int),
+                ("loc_id", ctypes.c_int), ("win32", ctypes.c_void_p), ("maxSize", ctypes.c_size_t),
+                ("usage", ctypes.c_ushort), ("reserved", ctypes.c_ubyte * 54)]
+
+
+@pytest.mark.parametrize("precision", ["c64", "c128"])
+def test_pooled_handle_equals_plain_handle(precision):
+    """A handle whose device memory comes from the caller's stream-ordered pool
+    (wp_create_pooled, what the server uses for admissions) gives the same bits as one
+    from wp_create, and gives its memory back to the pool."""
+    rt = _cudart()
+    dev = ctypes.c_int(0)
+    assert rt.cudaGetDevice(ctypes.byref(dev)) == 0
+    props = _PoolProps()
+    props.allocType = 1  # cudaMemAllocationTypePinned
+    props.loc_type = 1   # cudaMemLocationTypeDevice
+    props.loc_id = dev.value
+    pool = ctypes.c_void_p()
+    assert rt.cudaMemPoolCreate(ctypes.byref(pool), ctypes.byref(props)) == 0
+    try:
+        cfg = W.config_3d_barrier(n=64)
+        outs = []
+        for mp in (None, pool.value):
+            with WPK.Propagator(cfg["problem"], cfg["terms"], precision, autocorr=True, mem_pool=mp) as P:
+                P.init_gaussian(**cfg["init"])
+                obs = P.run(40, 20)
+                outs.append((P.get_state(), obs))
+        assert np.array_equal(outs[0][0], outs[1][0])
+        assert np.array_equal(WPK.obs_matrix(outs[0][1]), WPK.obs_matrix(outs[1][1]))
+        used = ctypes.c_uint64(0)
+        # cudaMemPoolAttrUsedMemCurrent = 7: nothing of the destroyed handle is still allocated
+        assert rt.cudaMemPoolGetAttribute(pool, 7, ctypes.byref(used)) == 0
+        assert used.value == 0
+    finally:
+        rt.cudaDeviceSynchronize()
+        rt.cudaMemPoolDestroy(pool)
