@@ -2,9 +2,11 @@
 // translation units of the complex64 and float-float forms.
 #pragma once
 
+#include <mutex>
 #include <type_traits>
 
 #include "wp_pass256.cuh"
+#include "wp_pass256_tma.cuh"
 
 namespace wp {
 namespace p256_detail {
@@ -44,6 +46,38 @@ void launch_contig_ng(const PassParams<T>& p, unsigned blocks, cudaStream_t st) 
     p256::k_pass256_contig<T, NG, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
 }
 
+// Tensor maps of the TMA-staged strided kernel: the state seen as rows of 2^log_inner
+// 8-byte points, box 16 x 256, 128-byte swizzle. cuTensorMapEncodeTiled comes from the
+// driver through the runtime's entry-point query (no link against the driver library).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline EncodeTiled encode_fn() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(f);
+    (void)cudaGetLastError();
+  });
+  return fn;
+}
+
+inline bool tile_map(EncodeTiled enc, const void* base, int log_inner, int lntot, CUtensorMap* m) {
+  const cuuint64_t dims[2] = {cuuint64_t(1) << log_inner, cuuint64_t(1) << (lntot - log_inner)};
+  const cuuint64_t strides[1] = {(cuuint64_t(1) << log_inner) * 8};
+  const cuuint32_t box[2] = {16, 256};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void*>(base), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <class T>
 int launch(const PassParams<T>& p, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -60,10 +94,27 @@ int launch(const PassParams<T>& p, void* stream) {
       launch_contig_ng<T, 1>(q, blocks, st);
     else
       launch_contig_ng<T, 0>(q, blocks, st);
-  } else if (p.flags & F_KIN) {
-    p256::k_pass256_strided<T, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
   } else {
-    p256::k_pass256_strided<T, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+    // complex64: the tile moved by the TMA (same arithmetic); the thread-staged kernel
+    // where no tensor map can be made
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      const EncodeTiled enc = encode_fn();
+      alignas(64) CUtensorMap tin, tout;
+      if (enc && tile_map(enc, p.in, p.log_inner, lntot, &tin) && tile_map(enc, p.out, p.log_inner, lntot, &tout)) {
+        if (p.flags & F_KIN)
+          p256::k_pass256_strided_tma<true><<<blocks, 256, p256::kTmaSmem, st>>>(p, tin, tout);
+        else
+          p256::k_pass256_strided_tma<false><<<blocks, 256, p256::kTmaSmem, st>>>(p, tin, tout);
+        done = true;
+      }
+    }
+    if (!done) {
+      if (p.flags & F_KIN)
+        p256::k_pass256_strided<T, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+      else
+        p256::k_pass256_strided<T, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+    }
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? 0 : (int)e;
