@@ -73,6 +73,7 @@ struct wp_handle {
   AxisTab<ff> tabff[3]{};
   double* part_pos = nullptr;
   double* part_mom = nullptr;
+  int64_t rows_pos = 0, rows_mom = 0;  // rows the last position / momentum sums wrote
   void* lines_phase = nullptr;     // LineRec<T>[N / n_last] (potential phase, per step)
   void* lines_kin[2] = {nullptr, nullptr};  // LineRec<T>[N / n_0] (kinetic factor dt, dt/2)
   int64_t nlines_phase = 0, nlines_kin = 0;
@@ -603,6 +604,13 @@ wp_status run_pass(wp_handle* h, int axis, uint32_t flags, void* in, void* out, 
   const PassParams<T> p = pass_params<T>(h, axis, flags, in, out, partials, khalf);
   int cls = (axis == h->ndim - 1) ? K_PASS_CONTIG : (flags & F_KIN) ? K_PASS_KIN : K_PASS_STRIDED;
   if (axis == 0 && (flags & F_OBS_MOM)) cls = K_PASS_STRIDED;
+  if (flags & (F_OBS_POS | F_OBS_MOM)) {
+    // the partial rows the record's reduction reads: one per block of the kernel chosen
+    int64_t rows = h->plan[axis].ntiles;
+    if constexpr (!std::is_same<T, double>::value)
+      if (pass256_applies<T>(p)) rows = pass256_blocks<T>(p);
+    (flags & F_OBS_POS ? h->rows_pos : h->rows_mom) = rows;
+  }
   LaunchScope ls(h, cls);
   return launch_rc(h, launch_pass<T>(p, h->plan[axis].ntiles, h->plan[axis].smem, h->stream), "pass kernel");
 }
@@ -853,15 +861,20 @@ wp_status momentum_and_reduce(wp_handle* h) {
     return st;
   ReduceParams r{};
   r.pos = h->part_pos;
-  r.npos = h->plan[nd - 1].ntiles;
+  r.npos = h->rows_pos;
   r.mom = h->part_mom;
-  r.nmom = h->plan[0].ntiles;
+  r.nmom = h->rows_mom;
   r.g = h->g;
   r.ntotal = h->N;
   r.autocorr = h->pb.autocorr ? 1 : 0;
   r.ctrl = h->ctrl;
   r.obs_out = h->obs_dev;
   r.obs_cap = h->obs_cap;
+  r.pos_stride = r.mom_stride = 1;
+  if (std::max(r.npos, r.nmom) > 512) {
+    LaunchScope ls(h, K_REDUCE);
+    if ((st = launch_rc(h, launch_reduce_rows(r, h->stream), "reduce kernel")) != WP_OK) return st;
+  }
   LaunchScope ls(h, K_REDUCE);
   return launch_rc(h, launch_reduce(r, h->stream), "reduce kernel");
 }

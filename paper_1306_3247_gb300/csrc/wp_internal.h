@@ -301,10 +301,11 @@ struct GridPhaseParams {
 };
 
 struct ReduceParams {
-  const double* pos;   // [npos][NQ]
+  const double* pos;   // [npos][NQ], rows pos_stride apart
   int64_t npos;
-  const double* mom;   // [nmom][NQ]
+  const double* mom;   // [nmom][NQ], rows mom_stride apart
   int64_t nmom;
+  int64_t pos_stride, mom_stride;
   Geom g;
   int64_t ntotal;      // grid points
   int32_t autocorr;
@@ -349,6 +350,10 @@ template <class T> int launch_prep_batch(const PrepParams<T>* params, int ninst,
                                          double tau_dt, void* stream);
 template <class T> int launch_res1d_batch(const Res1dParams<T>* params, int ninst, int nthreads, int ept,
                                           int64_t nsteps, size_t smem, void* stream);
+// The record's reduction in two launches: launch_reduce_rows sums fixed runs of partial
+// rows in place (adjusting p to the remaining rows; a no-op for few rows), launch_reduce
+// sums the rest and writes the record.
+int launch_reduce_rows(ReduceParams& p, void* stream);
 int launch_reduce(const ReduceParams& p, void* stream);
 template <class T> int launch_static_phase(const StaticPhaseParams<T>& p, void* stream);
 template <class T> int launch_grid_phase(const GridPhaseParams<T>& p, void* stream);
@@ -386,6 +391,7 @@ int launch_merged_strided(const PassParams<T>* params, const int64_t* tile_start
 // two-stage kernels for 256-point lines, complex64 and float-float (wp_pass256_*.cu)
 template <class T> bool pass256_applies(const PassParams<T>& p);
 template <class T> int launch_pass256(const PassParams<T>& p, void* stream);
+template <class T> int64_t pass256_blocks(const PassParams<T>& p);  // blocks (partial rows) of a launch
 // complex64 two-stage kernels for 64- and 128-point lines (wp_pass2s_f32.cu), single and
 // batched (class keys kBatchClassP2S + 100 (logn - 6) + v, v as for the 256-point class)
 constexpr int kBatchClassP2S = 1100;

@@ -653,6 +653,15 @@ __device__ __forceinline__ cx<float> apply_gauss_phase(cx<float> v, float th) {
   return cadd(v, cmul(v, g));
 }
 
+// A Gaussian term whose line coefficient g is below the level where apply_gauss_phase
+// leaves a point as it is (FP64 |theta| < 2^-60, float-float 2^-56, FP32 2^-25) gives every
+// point of the line such a phase (theta = g x axis factor, and the axis factors are at most
+// 1): the whole line can skip that term, with the same result. For a localised barrier that
+// is almost every line.
+__device__ __forceinline__ bool gauss_line_active(double g) { return fabs(g) >= 0x1p-60; }
+__device__ __forceinline__ bool gauss_line_active(float g) { return fabsf(g) >= 0x1p-25f; }
+__device__ __forceinline__ bool gauss_line_active(ff g) { return fabsf(g.hi) >= 0x1p-57f; }
+
 // Record forms of apply_factor (fixed-size kernels).
 __device__ __forceinline__ cx<double> apply_factor_rec(cx<double> v, const TwE<double>& a, const TwE<double>& L) {
   return cmul(v, cmul(a.w, L.w));
@@ -794,13 +803,60 @@ __device__ __forceinline__ void fixed_load(const PassParams<T>& p, cx<T>* s, int
   for (int k = 0; k < 8; k++) s[(i0 + k * ISTEP) * SH::LS + l] = v[k];
 }
 
+// One line's part of the 16 observable sums in FP64 (Tab. 3 quantities), from its sums
+// lt[0..7] over the pass axis (position pass: |psi|^2 times 1, x, x^2, the additive
+// potential, the Gaussian axis factors, and <psi0|psi>; momentum pass: |psi_hat|^2 times
+// 1, k, k^2) and its grid index gi on the other axes: the pass-axis moments come from the
+// line sums, the other axes' coordinates, wavenumbers, potential parts and Gaussian
+// factors are constant along the line (the potential is a sum of per-axis parts and
+// products of per-axis Gaussian factors).
+template <class T>
+__device__ __forceinline__ void obs_line_row(const PassParams<T>& p, const double (&lt)[8], const int (&gi)[3],
+                                             double* c) {
+  const int ax = p.axis;
+  for (int k = 0; k < NQ; k++) c[k] = 0.0;
+  if (p.flags & F_OBS_POS) {
+    c[Q_RHO] = lt[0];
+    const double xs = p.g.oscale_x[ax];  // the tables hold x / xs
+    c[Q_X + ax] = lt[1] * xs;
+    c[Q_XX + ax] = lt[2] * (xs * xs);
+    double A = 0.0;
+    for (int d = 0; d < p.g.ndim; d++) {
+      if (d == ax) continue;
+      const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
+      c[Q_X + d] = x * lt[0];
+      c[Q_XX + d] = x * x * lt[0];
+      A += p.A[d][gi[d]];
+    }
+    double v = lt[3] + A * lt[0];
+    for (int gg = 0; gg < p.ngauss; gg++) {
+      double prod = p.ctrl->gcoef[gg];
+      for (int d = 0; d < p.g.ndim; d++)
+        if (d != ax) prod *= p.Gd[gg][d][gi[d]];
+      v += prod * lt[4 + gg];
+    }
+    c[Q_V] = v;
+    c[Q_AC_RE] = lt[6];
+    c[Q_AC_IM] = lt[7];
+  } else {
+    c[Q_RHOK] = lt[0];
+    const double ks = p.g.oscale_k[ax];  // the tables hold k / ks
+    c[Q_K + ax] = lt[1] * ks;
+    double k2 = 0.0;
+    for (int d = 0; d < p.g.ndim; d++) {
+      if (d == ax) continue;
+      const double k = wavenumber(p.g, d, gi[d]);
+      c[Q_K + d] = k * lt[0];
+      k2 += k * k;
+    }
+    c[Q_K2] = lt[2] * (ks * ks) + k2 * lt[0];
+  }
+}
+
 // Block partials of the observable sums in a fixed-size kernel. Thread t holds the sums
 // of line l = t mod C over its 8 points (q[0..7], in T). The lanes of a line are combined
-// by xor shuffles, the 8 warps through the tile buffer, in a fixed order. Each line then
-// adds its part of the 16 sums in FP64: the pass-axis moments come from the line sums,
-// the other axes' coordinates, wavenumbers, potential parts and Gaussian factors are
-// constant along the line (Tab. 3 quantities; the potential is a sum of per-axis parts
-// and products of per-axis Gaussian factors). Partials of block b go to partials[b].
+// by xor shuffles, the 8 warps through the tile buffer, in a fixed order; each line adds
+// its row (obs_line_row). Partials of block b go to partials[b].
 template <class T, class SH>
 __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[8], int64_t o0, int64_t cb,
                                                  T* scratch, double (*red)[NQ]) {
@@ -828,50 +884,12 @@ __device__ __forceinline__ void fixed_obs_reduce(const PassParams<T>& p, T (&q)[
     for (int j = 0; j < 8; j++) lt[j] = red[tid][j];
   __syncthreads();
   if (tid < C) {
-    const int l = tid, ax = p.axis;
-    double* c = red[l];
-    for (int k = 0; k < NQ; k++) c[k] = 0.0;
     int gi[3];
     if (SH::contig)
-      grid_index(p.g, ax, o0 + l, 0, 0, gi);
+      grid_index(p.g, p.axis, o0 + tid, 0, 0, gi);
     else
-      grid_index(p.g, ax, o0, cb + l, 0, gi);
-    if (p.flags & F_OBS_POS) {
-      c[Q_RHO] = lt[0];
-      const double xs = p.g.oscale_x[ax];  // the tables hold x / xs
-      c[Q_X + ax] = lt[1] * xs;
-      c[Q_XX + ax] = lt[2] * (xs * xs);
-      double A = 0.0;
-      for (int d = 0; d < p.g.ndim; d++) {
-        if (d == ax) continue;
-        const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
-        c[Q_X + d] = x * lt[0];
-        c[Q_XX + d] = x * x * lt[0];
-        A += p.A[d][gi[d]];
-      }
-      double v = lt[3] + A * lt[0];
-      for (int gg = 0; gg < p.ngauss; gg++) {
-        double prod = p.ctrl->gcoef[gg];
-        for (int d = 0; d < p.g.ndim; d++)
-          if (d != ax) prod *= p.Gd[gg][d][gi[d]];
-        v += prod * lt[4 + gg];
-      }
-      c[Q_V] = v;
-      c[Q_AC_RE] = lt[6];
-      c[Q_AC_IM] = lt[7];
-    } else {
-      c[Q_RHOK] = lt[0];
-      const double ks = p.g.oscale_k[ax];  // the tables hold k / ks
-      c[Q_K + ax] = lt[1] * ks;
-      double k2 = 0.0;
-      for (int d = 0; d < p.g.ndim; d++) {
-        if (d == ax) continue;
-        const double k = wavenumber(p.g, d, gi[d]);
-        c[Q_K + d] = k * lt[0];
-        k2 += k * k;
-      }
-      c[Q_K2] = lt[2] * (ks * ks) + k2 * lt[0];
-    }
+      grid_index(p.g, p.axis, o0, cb + tid, 0, gi);
+    obs_line_row(p, lt, gi, red[tid]);
   }
   __syncthreads();
   if (tid < NQ) {
@@ -940,6 +958,8 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
           gstep = es * ISTEP;
         }
       }
+      const bool g0 = ph && p.ngauss > 0 && gauss_line_active(rec.g[0]);
+      const bool g1 = ph && p.ngauss > 1 && gauss_line_active(rec.g[1]);
 #pragma unroll
       for (int k = 0; k < 8; k++) {
         const int i = i0 + k * ISTEP;
@@ -947,8 +967,8 @@ __device__ __forceinline__ void pass_compute(const PassParams<T>& p, const SH& s
         if (ph) {
           // without additive terms the factors are exactly 1 and the product is skipped
           if (p.sep) v = apply_factor_rec(v, p.Prec[i], rec.L);
-          if (p.ngauss > 0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
-          if (p.ngauss > 1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
+          if (g0) v = apply_gauss_phase(v, rec.g[0] * G0[i]);
+          if (g1) v = apply_gauss_phase(v, rec.g[1] * G1[i]);
           s[i * LS + l] = v;
         }
         if constexpr (OBS) {
@@ -1755,7 +1775,36 @@ __global__ void __launch_bounds__((1 << LOGN) / EPT)
 
 #ifdef WP_COMMON_KERNELS
 // ------------------------------------------------------------------ reduction kernel
-// One block: sums the per-CTA partials in a fixed order and writes the observable record.
+// First level: block (b, y) sums rows [b R, b R + R) of the position (y = 0) or momentum
+// (y = 1) partials in a fixed order and leaves the sum in row b R, which no other block
+// reads. The sums are then in rows 0, R, 2R, ... (the partials are scratch of one record).
+__global__ void __launch_bounds__(256) k_reduce_rows(double* pos, int64_t npos, double* mom, int64_t nmom,
+                                                     int64_t R) {
+  __shared__ double red[32][NQ];
+  __shared__ double tot[NQ];
+  double* a = blockIdx.y ? mom : pos;
+  const int64_t n = blockIdx.y ? nmom : npos;
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  if (r0 >= n) return;  // the whole block leaves
+  const int64_t r1 = r0 + R < n ? r0 + R : n;
+  double acc[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; q++) acc[q] = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const double2* row = reinterpret_cast<const double2*>(a + r * NQ);
+#pragma unroll
+    for (int q = 0; q < NQ / 2; q++) {
+      const double2 v = row[q];
+      acc[2 * q] += v.x;
+      acc[2 * q + 1] += v.y;
+    }
+  }
+  block_sum(acc, tot, red);  // every thread has read its rows before the first barrier in it
+  if (threadIdx.x < NQ) a[r0 * NQ + threadIdx.x] = tot[threadIdx.x];
+}
+
+// One block: sums the (first-level) partials in a fixed order and writes the observable
+// record.
 __global__ void __launch_bounds__(256) k_reduce(const ReduceParams p) {
   __shared__ double red[32][NQ];
   __shared__ double qp[NQ], qm[NQ];
@@ -1763,12 +1812,14 @@ __global__ void __launch_bounds__(256) k_reduce(const ReduceParams p) {
 #pragma unroll
   for (int q = 0; q < NQ; q++) acc[q] = 0.0;
   for (int64_t r = threadIdx.x; r < p.npos; r += blockDim.x)
-    for (int q = 0; q < NQ; q++) acc[q] += p.pos[r * NQ + q];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] += p.pos[r * p.pos_stride * NQ + q];
   block_sum(acc, qp, red);
 #pragma unroll
   for (int q = 0; q < NQ; q++) acc[q] = 0.0;
   for (int64_t r = threadIdx.x; r < p.nmom; r += blockDim.x)
-    for (int q = 0; q < NQ; q++) acc[q] += p.mom[r * NQ + q];
+#pragma unroll
+    for (int q = 0; q < NQ; q++) acc[q] += p.mom[r * p.mom_stride * NQ + q];
   block_sum(acc, qm, red);
   if (threadIdx.x == 0) {
     const int64_t slot = p.ctrl->nobs;

@@ -190,12 +190,7 @@ __device__ __forceinline__ void load_twiddles(TwE<T>* s_tw, const void* W256) {
 __device__ __forceinline__ float table_value(const float* p) { return __ldg(p); }
 __device__ __forceinline__ ff table_value(const ff* p) { return *p; }
 
-// A Gaussian term whose line coefficient is below the level where apply_gauss_phase
-// leaves a point as it is (complex64: |theta| < 2^-25; float-float: 2^-56) gives every
-// point of the line such a phase (its axis factors are at most 1): the whole line skips
-// that term, with the same result. For a localised barrier that is almost every line.
-__device__ __forceinline__ bool gauss_line_active(float g) { return fabsf(g) >= 0x1p-25f; }
-__device__ __forceinline__ bool gauss_line_active(ff g) { return fabsf(g.hi) >= 0x1p-57f; }
+// Gaussian terms skip whole lines whose coefficient is negligible (gauss_line_active).
 
 // A factor that is the product of a line factor L (the other axes) and an axis factor a:
 // complex64 forms the product a L exactly (error-free products and sums of the high + low
@@ -243,10 +238,149 @@ __device__ __forceinline__ void kinetic256(const PassParams<T>& p, cx<T> (&v)[16
   fft256<true>(v, buf, tw, t);
 }
 
+// Observable sums of a two-stage pass (complex64; the tables and the per-line rows of the
+// Stockham kernels' sums). Position sums of the thread's 16 points (after the potential
+// phase): |psi|^2 times 1, x, x^2, the additive potential, the Gaussian axis factors,
+// and conj(psi0) psi (psi0: the thread's first point of the initial state).
+template <class T>
+__device__ __forceinline__ void pos_sums256(const PassParams<T>& p, const cx<T> (&v)[16], const cx<T>* psi0, int t,
+                                            T (&q)[8]) {
+  const T* G0 = p.G[0][p.axis];
+  const T* G1 = p.G[1][p.axis];
+  const bool ac = (p.flags & F_AUTOCORR) != 0;
+#pragma unroll
+  for (int r = 0; r < 16; r++) {
+    const int i = t + 16 * r;
+    const T rho = norm2(v[r]);
+    const cx<T> xx = p.Ox[i];
+    q[0] = q[0] + rho;
+    q[1] = madd(xx.re, rho, q[1]);
+    q[2] = madd(xx.im, rho, q[2]);
+    q[3] = madd(p.AT[i], rho, q[3]);
+    if (p.ngauss > 0) q[4] = madd(G0[i], rho, q[4]);
+    if (p.ngauss > 1) q[5] = madd(G1[i], rho, q[5]);
+    if (ac) {
+      const cx<T> c = cmulc(v[r], psi0[16 * r]);
+      q[6] = q[6] + c.re;
+      q[7] = q[7] + c.im;
+    }
+  }
+}
+
+// Momentum sums of the thread's 16 points after the forward transform: |psi_hat|^2 times
+// 1, k, k^2.
+template <class T>
+__device__ __forceinline__ void mom_sums256(const PassParams<T>& p, const cx<T> (&v)[16], int t, T (&q)[8]) {
+#pragma unroll
+  for (int r = 0; r < 16; r++) {
+    const T rho = norm2(v[r]);
+    const cx<T> kk = p.Ok[t + 16 * r];
+    q[0] = q[0] + rho;
+    q[1] = madd(kk.re, rho, q[1]);
+    q[2] = madd(kk.im, rho, q[2]);
+  }
+}
+
+// The block's partial row. The 16 threads of a line combine their sums by xor
+// butterflies (every lane then holds the line sums) and lane t forms slot t of the line's
+// FP64 row, the row obs_line_row forms in one thread: lanes 0..2 first load the additive
+// potential part of axis t, lanes 4 and 5 the product of Gaussian term t - 4's factors on
+// the other axes, and the slots gather them by shuffles, so that the line's loads are
+// issued together. o, c: the line's outer index and column, as grid_index takes them.
+// The block's lines are then summed in order into partials[blockIdx.x]. Every thread of
+// the block calls it.
+template <class T>
+__device__ __forceinline__ void obs256_partials(const PassParams<T>& p, T (&q)[8], int64_t o, int64_t c, int l,
+                                                int t) {
+  static_assert(NQ == 16, "one row slot per lane of a line");
+  __shared__ double red[lines_of<T>()][NQ];
+#pragma unroll
+  for (int s = 8; s > 0; s >>= 1)
+#pragma unroll
+    for (int j = 0; j < 8; j++) q[j] = q[j] + shfl_xor(q[j], s);
+  const int ax = p.axis, nd = p.g.ndim;
+  const bool pos = (p.flags & F_OBS_POS) != 0;
+  int gi[3];
+  grid_index(p.g, ax, o, c, 0, gi);
+  double part = 0.0;
+  if (pos) {
+    if (t < nd && t != ax) {
+      part = p.A[t][gi[t]];
+    } else if (t >= 4 && t - 4 < p.ngauss) {
+      const int gg = t - 4;
+      double prod = p.ctrl->gcoef[gg];
+      for (int d = 0; d < nd; d++)
+        if (d != ax) prod *= p.Gd[gg][d][gi[d]];
+      part = prod;
+    }
+  }
+  const double A = (__shfl_sync(0xffffffffu, part, 0, 16) + __shfl_sync(0xffffffffu, part, 1, 16)) +
+                   __shfl_sync(0xffffffffu, part, 2, 16);
+  const double P0 = __shfl_sync(0xffffffffu, part, 4, 16);
+  const double P1 = __shfl_sync(0xffffffffu, part, 5, 16);
+  double v = 0.0;
+  if (pos) {
+    const double xs = p.g.oscale_x[ax];  // the tables hold x / xs
+    if (t == Q_RHO) {
+      v = to_f64(q[0]);
+    } else if (t >= Q_X && t < Q_X + 3) {
+      const int d = t - Q_X;
+      if (d == ax)
+        v = to_f64(q[1]) * xs;
+      else if (d < nd)
+        v = (p.g.xmin[d] + (double)gi[d] * p.g.dx[d]) * to_f64(q[0]);
+    } else if (t >= Q_XX && t < Q_XX + 3) {
+      const int d = t - Q_XX;
+      if (d == ax) {
+        v = to_f64(q[2]) * (xs * xs);
+      } else if (d < nd) {
+        const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
+        v = x * x * to_f64(q[0]);
+      }
+    } else if (t == Q_V) {
+      v = to_f64(q[3]) + A * to_f64(q[0]);
+      if (p.ngauss > 0) v += P0 * to_f64(q[4]);
+      if (p.ngauss > 1) v += P1 * to_f64(q[5]);
+    } else if (t == Q_AC_RE) {
+      v = to_f64(q[6]);
+    } else if (t == Q_AC_IM) {
+      v = to_f64(q[7]);
+    }
+  } else {
+    const double ks = p.g.oscale_k[ax];  // the tables hold k / ks
+    if (t == Q_RHOK) {
+      v = to_f64(q[0]);
+    } else if (t >= Q_K && t < Q_K + 3) {
+      const int d = t - Q_K;
+      if (d == ax)
+        v = to_f64(q[1]) * ks;
+      else if (d < nd)
+        v = wavenumber(p.g, d, gi[d]) * to_f64(q[0]);
+    } else if (t == Q_K2) {
+      double k2 = 0.0;
+      for (int d = 0; d < nd; d++) {
+        if (d == ax) continue;
+        const double k = wavenumber(p.g, d, gi[d]);
+        k2 += k * k;
+      }
+      v = to_f64(q[2]) * (ks * ks) + k2 * to_f64(q[0]);
+    }
+  }
+  red[l][t] = v;
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    double sum = 0.0;
+    for (int k = 0; k < lines_of<T>(); k++) sum += red[k][threadIdx.x];
+    p.partials[blockIdx.x * (int64_t)NQ + threadIdx.x] = sum;
+  }
+}
+
 // Contiguous axis: tile b is lines L b .. L b + L - 1 (L lines per block); warp w serves
-// lines L b + 2 w + g. Flags: F_IFFT, F_PHASE, F_FFT (any subset, in that order). v: the
-// thread's 16 points of its line, already loaded by the caller.
-template <int NG, bool SEP, class T>
+// lines L b + 2 w + g. Flags: F_IFFT, F_PHASE, F_FFT (any subset, in that order); with
+// OBS also F_OBS_POS (position sums after the phase, before the forward transform),
+// F_AUTOCORR and F_NO_STORE. v: the thread's 16 points of its line, already loaded by the
+// caller.
+template <int NG, bool SEP, bool OBS = false, class T>
 __device__ __forceinline__ void contig_body(const PassParams<T>& p, int64_t tile, unsigned char* smem,
                                             cx<T> (&v)[16]) {
   TwE<T>* s_tw = reinterpret_cast<TwE<T>*>(smem);
@@ -264,10 +398,19 @@ __device__ __forceinline__ void contig_body(const PassParams<T>& p, int64_t tile
     const LineRec<T> rec = p.lines_phase[line];
     phase256<NG, SEP>(p, v, rec, t);
   }
-  if (f & F_FFT) fft256<false>(v, buf, s_tw, t);
-  cx<T>* dst = p.out + (line << kLogN) + t;
+  [[maybe_unused]] T q[8];
+  if constexpr (OBS) {
 #pragma unroll
-  for (int r = 0; r < 16; r++) dst[16 * r] = v[r];
+    for (int j = 0; j < 8; j++) q[j] = T(0);
+    if (f & F_OBS_POS) pos_sums256(p, v, p.psi0 + (line << kLogN) + t, t, q);
+  }
+  if (f & F_FFT) fft256<false>(v, buf, s_tw, t);
+  if (!(OBS && (f & F_NO_STORE))) {
+    cx<T>* dst = p.out + (line << kLogN) + t;
+#pragma unroll
+    for (int r = 0; r < 16; r++) dst[16 * r] = v[r];
+  }
+  if constexpr (OBS) obs256_partials(p, q, line, 0, l, t);
 }
 
 // The 16 points t + 16 r of the thread's line of a contiguous tile.
@@ -308,7 +451,9 @@ __device__ __forceinline__ void strided_load(const cx<T>* in, int log_inner, int
   for (int q = 0; q < Stage<T>::Q; q++) ld[q] = __ldg(reinterpret_cast<const float4*>(gin + q * rstep));
 }
 
-template <bool KIN, class T>
+// OBS (complex64, forward transform only): the momentum sums after the transform, and
+// F_NO_STORE.
+template <bool KIN, bool OBS = false, class T>
 __device__ __forceinline__ void strided_body(const PassParams<T>& p, int64_t o, int64_t cb, unsigned char* smem,
                                              const float4 (&ld)[Stage<T>::Q]) {
   using S = Stage<T>;
@@ -342,6 +487,16 @@ __device__ __forceinline__ void strided_body(const PassParams<T>& p, int64_t o, 
   } else {
     fft256<false>(v, reg, s_tw, t);
   }
+  [[maybe_unused]] T qs[8];
+  if constexpr (OBS) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) qs[j] = T(0);
+    mom_sums256(p, v, t, qs);
+    if (p.flags & F_NO_STORE) {
+      obs256_partials(p, qs, o, cb + l, l, t);
+      return;
+    }
+  }
   __syncwarp();  // the last transpose's reads of the region are done
 #pragma unroll
   for (int r = 0; r < 16; r++) reg[t + 16 * r] = v[r];
@@ -360,27 +515,29 @@ __device__ __forceinline__ void strided_body(const PassParams<T>& p, int64_t o, 
     }
     *reinterpret_cast<float4*>(gout + q * rstep) = w;
   }
+  if constexpr (OBS) obs256_partials(p, qs, o, cb + l, l, t);
 }
 
 // NG Gaussian terms, SEP additive terms in the potential (one kernel per kind keeps the
 // unrolled phase code small).
-template <class T, int NG, bool SEP>
+// OBS: the variant with the position sums (complex64).
+template <class T, int NG, bool SEP, bool OBS = false>
 __global__ void __launch_bounds__(threads_of<T>(), Shape<T>::kMinBlocks) k_pass256_contig(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the line loads are issued before the twiddle table's (their latencies overlap)
   cx<T> v[16];
   contig_load(p.in, blockIdx.x, v);
-  contig_body<NG, SEP>(p, blockIdx.x, smem_raw, v);
+  contig_body<NG, SEP, OBS>(p, blockIdx.x, smem_raw, v);
 }
 
-template <class T, bool KIN>
+template <class T, bool KIN, bool OBS = false>
 __global__ void __launch_bounds__(threads_of<T>(), Shape<T>::kMinBlocks) k_pass256_strided(const PassParams<T> p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int64_t o, cb;
   strided_origin<T>(p.log_inner, blockIdx.x, o, cb);
   float4 ld[Stage<T>::Q];
   strided_load(p.in, p.log_inner, o, cb, ld);
-  strided_body<KIN>(p, o, cb, smem_raw, ld);
+  strided_body<KIN, OBS>(p, o, cb, smem_raw, ld);
 }
 
 // Batched form: block-list entry blk is tile blk - tile_start[inst] of instance

@@ -15,13 +15,23 @@ template <class T>
 constexpr bool two_stage_strided() { return std::is_same<T, float>::value; }
 
 // The two-stage kernels serve a pass when: 256 points along the axis, the fixed-shape
-// schedule, no partial sums, no grid potential, and whole tiles (L lines of a contiguous
-// axis, L adjacent columns of a strided one; L = 16 complex64, 8 float-float).
+// schedule, no grid potential, whole tiles (L lines of a contiguous axis, L adjacent
+// columns of a strided one; L = 16 complex64, 8 float-float), and partial sums only in
+// complex64: position sums on the contiguous axis, momentum sums after a forward
+// transform on a strided one.
 template <class T>
 bool applies(const PassParams<T>& p) {
   if (!p.fixed || p.logn != p256::kLogN || !p.W256) return false;
-  if (p.flags & (F_OBS_POS | F_OBS_MOM | F_NO_STORE | F_AUTOCORR)) return false;
-  if (p.grid_rec && (p.flags & F_PHASE)) return false;
+  const uint32_t f = p.flags;
+  if (f & (F_OBS_POS | F_OBS_MOM | F_NO_STORE | F_AUTOCORR)) {
+    if (!std::is_same<T, float>::value || !p.partials) return false;
+    if (p.log_inner == 0) {
+      if ((f & F_OBS_MOM) || !(f & F_OBS_POS) || p.grid_v) return false;
+    } else if ((f & (F_OBS_POS | F_AUTOCORR | F_KIN | F_IFFT)) || !(f & F_OBS_MOM) || !(f & F_FFT)) {
+      return false;
+    }
+  }
+  if (p.grid_rec && (f & F_PHASE)) return false;
   int lntot = 0;
   for (int d = 0; d < p.g.ndim; d++) lntot += p.g.ln[d];
   const int lines_log = lntot - p256::kLogN;
@@ -37,13 +47,24 @@ bool applies(const PassParams<T>& p) {
   return p.log_inner >= LL;
 }
 
-// The contiguous kernel of the potential's kind: Gaussian terms (0..2), additive terms.
+// The contiguous kernel of the potential's kind: Gaussian terms (0..2), additive terms;
+// the variant with position sums for complex64.
 template <class T, int NG>
 void launch_contig_ng(const PassParams<T>& p, unsigned blocks, cudaStream_t st) {
+  constexpr unsigned nt = p256::threads_of<T>();
+  if constexpr (std::is_same<T, float>::value) {
+    if (p.flags & F_OBS_POS) {
+      if (p.sep)
+        p256::k_pass256_contig<T, NG, true, true><<<blocks, nt, p256::kSmem, st>>>(p);
+      else
+        p256::k_pass256_contig<T, NG, false, true><<<blocks, nt, p256::kSmem, st>>>(p);
+      return;
+    }
+  }
   if (p.sep)
-    p256::k_pass256_contig<T, NG, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+    p256::k_pass256_contig<T, NG, true><<<blocks, nt, p256::kSmem, st>>>(p);
   else
-    p256::k_pass256_contig<T, NG, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+    p256::k_pass256_contig<T, NG, false><<<blocks, nt, p256::kSmem, st>>>(p);
 }
 
 // Tensor maps of the TMA-staged strided kernel: the state seen as rows of 2^log_inner
@@ -78,6 +99,14 @@ inline bool tile_map(EncodeTiled enc, const void* base, int log_inner, int lntot
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Blocks of a pass launch (one partial row each when it forms sums).
+template <class T>
+int64_t blocks_of(const PassParams<T>& p) {
+  int lntot = 0;
+  for (int d = 0; d < p.g.ndim; d++) lntot += p.g.ln[d];
+  return int64_t(1) << (lntot - p256::kLogN - p256::Shape<T>::kLogLines);
+}
+
 template <class T>
 int launch(const PassParams<T>& p, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -104,16 +133,21 @@ int launch(const PassParams<T>& p, void* stream) {
       if (enc && tile_map(enc, p.in, p.log_inner, lntot, &tin) && tile_map(enc, p.out, p.log_inner, lntot, &tout)) {
         if (p.flags & F_KIN)
           p256::k_pass256_strided_tma<true><<<blocks, 256, p256::kTmaSmem, st>>>(p, tin, tout);
+        else if (p.flags & F_OBS_MOM)
+          p256::k_pass256_strided_tma<false, true><<<blocks, 256, p256::kTmaSmem, st>>>(p, tin, tout);
         else
           p256::k_pass256_strided_tma<false><<<blocks, 256, p256::kTmaSmem, st>>>(p, tin, tout);
         done = true;
       }
     }
     if (!done) {
+      constexpr unsigned nt = p256::threads_of<T>();
       if (p.flags & F_KIN)
-        p256::k_pass256_strided<T, true><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+        p256::k_pass256_strided<T, true><<<blocks, nt, p256::kSmem, st>>>(p);
+      else if (std::is_same<T, float>::value && (p.flags & F_OBS_MOM))
+        p256::k_pass256_strided<T, false, std::is_same<T, float>::value><<<blocks, nt, p256::kSmem, st>>>(p);
       else
-        p256::k_pass256_strided<T, false><<<blocks, p256::threads_of<T>(), p256::kSmem, st>>>(p);
+        p256::k_pass256_strided<T, false><<<blocks, nt, p256::kSmem, st>>>(p);
     }
   }
   const cudaError_t e = cudaGetLastError();
@@ -157,6 +191,10 @@ int launch_batch(const PassParams<T>* params, const int64_t* tile_start, const i
   template <>                                                                                                  \
   bool pass256_applies<T>(const PassParams<T>& p) {                                                            \
     return p256_detail::applies<T>(p);                                                                         \
+  }                                                                                                            \
+  template <>                                                                                                  \
+  int64_t pass256_blocks<T>(const PassParams<T>& p) {                                                          \
+    return p256_detail::blocks_of<T>(p);                                                                       \
   }                                                                                                            \
   template <>                                                                                                  \
   int launch_pass256<T>(const PassParams<T>& p, void* stream) {                                                \

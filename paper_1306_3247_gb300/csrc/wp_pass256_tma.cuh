@@ -71,7 +71,9 @@ __device__ __forceinline__ uint32_t swz(int row, int c) {
 
 // tm_in / tm_out: 2-D maps of the state seen as rows of 2^log_inner points (8-byte
 // elements), box 16 x 256, 128-byte swizzle. Flags and tiles as k_pass256_strided.
-template <bool KIN>
+// OBS: the momentum sums after the forward transform (and F_NO_STORE), as
+// k_pass256_strided<float, false, true>.
+template <bool KIN, bool OBS = false>
 __global__ void __launch_bounds__(256, Shape<float>::kMinBlocks)
     k_pass256_strided_tma(const PassParams<float> p, const __grid_constant__ CUtensorMap tm_in,
                           const __grid_constant__ CUtensorMap tm_out) {
@@ -133,12 +135,23 @@ __global__ void __launch_bounds__(256, Shape<float>::kMinBlocks)
   } else {
     fft256<false>(v, reg, s_tw, t);
   }
+  [[maybe_unused]] float qs[8];
+  if constexpr (OBS) {
+#pragma unroll
+    for (int j = 0; j < 8; j++) qs[j] = 0.0f;
+    mom_sums256(p, v, t, qs);
+    if (p.flags & F_NO_STORE) {
+      obs256_partials(p, qs, o, cb + l, l, t);
+      return;
+    }
+  }
   __syncthreads();  // every transpose is done: back to the swizzled tile layout
 #pragma unroll
   for (int r = 0; r < 16; r++) *reinterpret_cast<cx<float>*>(tile + swz(t + 16 * r, l)) = v[r];
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
   if (threadIdx.x == 0) tma_store_2d(&tm_out, x, y, tile_s);
+  if constexpr (OBS) obs256_partials(p, qs, o, cb + l, l, t);
 }
 
 }  // namespace p256

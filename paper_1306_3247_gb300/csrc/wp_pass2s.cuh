@@ -113,8 +113,8 @@ template <int LOGT, int NG, bool SEP>
 __device__ __forceinline__ void phase(const PassParams<float>& p, cx<float> (&v)[8], const LineRec<float>& rec, int t) {
   const float* G0 = p.G[0][p.axis];
   const float* G1 = p.G[1][p.axis];
-  const bool g0 = NG > 0 && p256::gauss_line_active(rec.g[0]);
-  const bool g1 = NG > 1 && p256::gauss_line_active(rec.g[1]);
+  const bool g0 = NG > 0 && gauss_line_active(rec.g[0]);
+  const bool g1 = NG > 1 && gauss_line_active(rec.g[1]);
 #pragma unroll
   for (int r = 0; r < 8; r++) {
     const int i = t + (r << LOGT);
