@@ -1423,7 +1423,7 @@ wp_status batch_issue(wp_batch* b, int64_t m) {
                      "batched line records");
   };
   // One launch per pass over the merged classes (the kinetic one with the next step's
-  // tables as trailing blocks when asked: step increment, time shift, phase length in dt;
+  // tables as leading blocks when asked: step increment, time shift, phase length in dt;
   // tau 0 forms the tables without line records), then any class of its own.
   auto zmerged = [&](uint32_t f) -> wp_status {
     if (b->ml_z.ncls > 0) {

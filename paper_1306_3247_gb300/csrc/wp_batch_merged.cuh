@@ -1,7 +1,7 @@
 // One launch per pass of an uneven batch (the 2-D instances of wp_batch): the blocks of
 // the Stockham line-length classes of the pass run in the same grid, each block picking
 // its class from the launch's class table, and the per-instance tables and line records
-// of the next step (k_prep_batch and k_lines_batch work) run as trailing blocks of the
+// of the next step (k_prep_batch and k_lines_batch work) run as leading blocks of the
 // kinetic pass.
 // The kinetic pass reads neither the potential tables nor the line records of the
 // potential pass, and the potential pass that read the current ones has completed before
@@ -111,19 +111,22 @@ constexpr int merged_min_blocks() {
 }
 
 // CONTIG: the potential pass (axis 1) or the kinetic pass (axis 0). Launch blocks
-// ml.start[c] .. ml.start[c + 1] - 1 serve class c (block-list entries from
-// ml.list_off[c]); blocks from ml.start[ml.ncls] on form the tables of instance
-// (block - ml.start[ml.ncls]).
+// 0 .. ml.nprep - 1 form the tables of instance (block); the blocks after them serve the
+// classes: ml.nprep + ml.start[c] .. ml.nprep + ml.start[c + 1] - 1 class c (block-list
+// entries from ml.list_off[c]). The table blocks come first so that they are dispatched
+// first: their work is FP64 (the phase sincos), the pass blocks' FP32 and memory, and
+// the two run side by side on the SMs; as trailing blocks they formed the launch's tail
+// (ncu: FP64 pipe 37 % busy over the launch). No pass block reads what they write.
 template <class T, bool CONTIG>
 __global__ void __launch_bounds__(256, merged_min_blocks<T>())
     k_pass_batch_merged(const PassParams<T>* __restrict__ params, const int64_t* __restrict__ tile_start,
                         const int* __restrict__ block_inst, const MergedLaunch ml, uint32_t flags, int khalf,
                         const PrepParams<T>* __restrict__ pp, const LinesParams<T>* __restrict__ lp) {
-  const int64_t b = blockIdx.x;
-  if (b >= ml.start[ml.ncls]) {
-    prep_lines_block<T>(pp, lp, (int)(b - ml.start[ml.ncls]), ml);
+  if ((int64_t)blockIdx.x < ml.nprep) {
+    prep_lines_block<T>(pp, lp, (int)blockIdx.x, ml);
     return;
   }
+  const int64_t b = (int64_t)blockIdx.x - ml.nprep;
   __shared__ __align__(16) unsigned char raw[sizeof(PassParams<T>)];
   int c = 0;
   while (c + 1 < ml.ncls && b >= ml.start[c + 1]) c++;

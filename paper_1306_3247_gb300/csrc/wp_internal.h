@@ -365,9 +365,9 @@ template <class T> int pass_smem_limit_set(size_t smem);
 template <class T> int launch_fixed(const PassParams<T>& p, unsigned ntiles, size_t smem, void* stream);
 // One launch per batched pass (wp_batch_merged.cuh): class c of the pass covers launch
 // blocks start[c] .. start[c + 1] - 1 and block-list entries list_off[c] on; key[c] is its
-// line-length class (6..10 fixed-shape, kBatchClassP256 + v two-stage). nprep trailing
-// blocks form the per-instance tables (and, with lines, the line records) of the next
-// step, with the step increment, time shift and phase length (units of dt) given.
+// line-length class (6..10 fixed-shape, kBatchClassP256 + v two-stage), counted after nprep
+// leading blocks that form the per-instance tables (and, with lines, the line records) of
+// the next step, with the step increment, time shift and phase length (units of dt) given.
 constexpr int kMergedMaxClasses = 8;
 struct MergedLaunch {
   int32_t ncls;
