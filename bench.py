@@ -52,9 +52,9 @@ FP64_FLOP_PER_CLOCK_PER_SM = 4
 # ncu capture of the current kernels (dram__bytes_read.sum + dram__bytes_write.sum). Valid
 # for grid 256 only; any other grid reports null.
 TRAFFIC_256 = {
-    "c128": {"pass_contig": 479680256, "pass_strided": 471920640, "pass_kinetic": 477102848},
-    "c64": {"pass_contig": 210324480, "pass_strided": 209497344, "pass_kinetic": 214499840},
-    "c128f": {"pass_contig": 478073088, "pass_strided": 471793664, "pass_kinetic": 477358336},
+    "c128": {"pass_contig": 480336128, "pass_strided": 472172288, "pass_kinetic": 477476096},
+    "c64": {"pass_contig": 206836992, "pass_strided": 205500416, "pass_kinetic": 209300736},
+    "c128f": {"pass_contig": 474867456, "pass_strided": 471806464, "pass_kinetic": 477838592},
 }
 
 
@@ -67,7 +67,8 @@ def peaks():
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, ("fallback: 6.8 TB/s HBM, 1.9 PFLOP/s bf16 from one "
+                                                            "earlier GB300 measurement (no MEASURED_PEAKS.json)")
 
 
 class ClockSampler:
@@ -446,14 +447,14 @@ def main():
     if args.precision == "c128":
         # the FP64 pipe bounds this form: peak derived from the unit counts and the clock
         nsm = torch.cuda.get_device_properties(local).multi_processor_count
-        mhz = pk.get("sm_max_mhz") or 2070.0
+        mhz = pk.get("sm_max_mhz") or 2070.0  # else GB300's maximum SM clock
         fp64_peak = nsm * FP64_FLOP_PER_CLOCK_PER_SM * mhz * 1e6 / 1e12
         flops = pass_flops_per_point(logn, dom_name) * npts
         roof = {"bound": "alu", "kernel": dom_name, "achieved": flops / avg_s / 1e12, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": flops / avg_s / 1e12 / fp64_peak,
                 "traffic": traffic_of(args.grid, args.precision, dom_name),
                 "peak_source": f"derived: {nsm} SMs x 2 FP64 FMA per clock x 2 FLOP x {mhz:.0f} MHz "
-                               "(GB300 nominal FP64 1.25 TFLOP/s)",
+                               f"(GB300 nominal FP64 1.25 TFLOP/s); clock and HBM peak: {src}",
                 "probe_fp64_fma_tflops": probe_rate(WPK, True),
                 "probe_fp32_fma_tflops": probe_rate(WPK, False),
                 "avg_launch_ms": dom_v["avg_ms"], "launches": dom_v["launches"],
@@ -475,7 +476,7 @@ def main():
             el = 8 if form == "c64" else 16
             r["roofline"] = {"bound": "hbm", "kernel": kd[0],
                              "achieved": 2 * npts * el / (kd[1]["avg_ms"] / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                             "unit": "GB/s", "traffic": traffic_of(args.grid, form, kd[0])}
+                             "unit": "GB/s", "traffic": traffic_of(args.grid, form, kd[0]), "peak_source": src}
             r["roofline"]["frac"] = r["roofline"]["achieved"] / pk["hbm_gbs"]
             r["dtype"] = {"c128f": "f32x2", "c64": "f32"}[form]
             st = r.pop("state", None)
