@@ -551,6 +551,7 @@ PassParams<T> pass_params(wp_handle* h, int axis, uint32_t flags, void* in, void
   p.Ox = tb[axis].Ox;
   p.Ok = tb[axis].Ok;
   p.AT = tb[axis].AT;
+  for (int d = 0; d < 3; d++) p.ATax[d] = d < h->ndim ? tb[d].AT : nullptr;
   p.grid_v = h->vgrid;
   p.grid_rec = (h->vgrid && h->phase_half >= 0) ? (const TwE<T>*)h->vgrid_rec[h->phase_half] : nullptr;
   p.W256 = tb[axis].W256;
@@ -1640,6 +1641,14 @@ wp_status wp_create_pooled(const wp_problem* pb, void* stream, void* mem_pool, w
     const double xm = std::max(std::fabs(g.xmin[d]), std::fabs(g.xmin[d] + (double)(h->n[d] - 1) * g.dx[d]));
     g.oscale_x[d] = pow2_at_least(xm);
     g.oscale_k[d] = pow2_at_least(g.kscale[d] * (double)(h->n[d] / 2));
+  }
+  g.k2s = 1.0;
+  for (int d = 0; d < pb->ndim; d++) g.k2s = std::max(g.k2s, g.oscale_k[d] * g.oscale_k[d]);
+  for (int d = 0; d < 3; d++) {
+    g.xr0[d] = (float)(g.xmin[d] / g.oscale_x[d]);
+    g.dxr[d] = (float)(g.dx[d] / g.oscale_x[d]);
+    g.kr[d] = (float)(g.kscale[d] / g.oscale_k[d]);
+    g.k2r[d] = d < pb->ndim ? (float)(g.oscale_k[d] * g.oscale_k[d] / g.k2s) : 0.0f;
   }
   g.mass = pb->mass;
   g.hbar = pb->hbar;

@@ -131,6 +131,11 @@ struct Geom {
   // formed in FP32 range stay finite in any units (in SI units k^2 |psi_hat|^2 alone
   // exceeds the FP32 range); the FP64 combination multiplies the scale back, exactly.
   double oscale_x[3], oscale_k[3];
+  // Scaled FP32 geometry of the complex64 two-stage kernels' per-line observable rows:
+  // x_i / oscale_x = xr0 + i dxr, k_j / oscale_k = j kr (j the signed index),
+  // k2r = oscale_k^2 / k2s with k2s = the largest oscale_k^2 (powers of two: exact).
+  float xr0[3], dxr[3], kr[3], k2r[3];
+  double k2s;
 };
 
 // Device tables of one axis for precision T.
@@ -200,6 +205,7 @@ struct PassParams {
   const cx<T>* Ox;     // pass-axis observable tables (fixed-size kernels)
   const cx<T>* Ok;
   const T* AT;
+  const T* ATax[3];    // A(x,t) rounded to T on every axis (two-stage kernels' line rows)
   const TwE<T>* grid_rec;  // static grid potential: phase records of this pass's tau, or NULL
   const double* grid_v;    // static grid potential (observables), or NULL
   const void* W256;        // two-stage 256-point kernels: twiddle records of the pass axis, or NULL

@@ -283,95 +283,103 @@ __device__ __forceinline__ void mom_sums256(const PassParams<T>& p, const cx<T> 
 
 // The block's partial row. The 16 threads of a line combine their sums by xor
 // butterflies (every lane then holds the line sums) and lane t forms slot t of the line's
-// FP64 row, the row obs_line_row forms in one thread: lanes 0..2 first load the additive
-// potential part of axis t, lanes 4 and 5 the product of Gaussian term t - 4's factors on
-// the other axes, and the slots gather them by shuffles, so that the line's loads are
-// issued together. o, c: the line's outer index and column, as grid_index takes them.
-// The block's lines are then summed in order into partials[blockIdx.x]. Every thread of
-// the block calls it.
+// row (the quantities obs_line_row forms in FP64 for the Stockham kernels), in FP32 and
+// scaled so that no product leaves the FP32 range in any units: slot t holds its value
+// divided by a power of two s_t that is the same for every line (oscale_x[d] or its
+// square for the position moments of axis d, oscale_k[d] for the momentum of axis d,
+// k2s for |k|^2). The block's lines are then summed in order in FP64 and multiplied by
+// s_t (exactly) into partials[blockIdx.x]. The row is formed in FP32 because GB300 runs
+// FP64 at 1/64 of the FP32 rate: an FP64 row, one branch per slot, made the observable
+// passes 25-70 us longer than the plain ones on the 256^3 grid. o, c: the line's outer
+// index and column, as grid_index takes them. Every thread of the block calls it.
 template <class T>
 __device__ __forceinline__ void obs256_partials(const PassParams<T>& p, T (&q)[8], int64_t o, int64_t c, int l,
                                                 int t) {
+  static_assert(std::is_same<T, float>::value, "the two-stage kernels form sums in complex64 only");
   static_assert(NQ == 16, "one row slot per lane of a line");
-  __shared__ double red[lines_of<T>()][NQ];
+  __shared__ float red[lines_of<T>()][NQ];
 #pragma unroll
   for (int s = 8; s > 0; s >>= 1)
 #pragma unroll
     for (int j = 0; j < 8; j++) q[j] = q[j] + shfl_xor(q[j], s);
-  const int ax = p.axis, nd = p.g.ndim;
+  const Geom& g = p.g;
+  const int ax = p.axis, nd = g.ndim;
   const bool pos = (p.flags & F_OBS_POS) != 0;
   int gi[3];
-  grid_index(p.g, ax, o, c, 0, gi);
-  double part = 0.0;
+  grid_index(g, ax, o, c, 0, gi);
+  const float lt0 = q[0];
+  float v = 0.0f;
   if (pos) {
-    if (t < nd && t != ax) {
-      part = p.A[t][gi[t]];
-    } else if (t >= 4 && t - 4 < p.ngauss) {
-      const int gg = t - 4;
-      double prod = p.ctrl->gcoef[gg];
-      for (int d = 0; d < nd; d++)
-        if (d != ax) prod *= p.Gd[gg][d][gi[d]];
-      part = prod;
+    // slots Q_X + d and Q_XX + d
+    const bool sq = t >= Q_XX && t < Q_XX + 3;
+    const int d = sq ? t - Q_XX : (t >= Q_X && t < Q_X + 3 ? t - Q_X : 0);
+    const int gd = d == 0 ? gi[0] : (d == 1 ? gi[1] : gi[2]);
+    const float xr = fmaf((float)gd, d == 0 ? g.dxr[0] : (d == 1 ? g.dxr[1] : g.dxr[2]),
+                          d == 0 ? g.xr0[0] : (d == 1 ? g.xr0[1] : g.xr0[2]));
+    const float mom = d == ax ? (sq ? q[2] : q[1]) : (sq ? xr * xr : xr) * lt0;
+    // the line's potential parts on the other axes
+    float A = 0.0f, P0 = 0.0f, P1 = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 3; e++)
+      if (e < nd && e != ax) A += p.ATax[e][gi[e]];
+    if (p.ngauss > 0) {
+      P0 = (float)p.ctrl->gcoef[0];
+#pragma unroll
+      for (int e = 0; e < 3; e++)
+        if (e < nd && e != ax) P0 *= p.G[0][e][gi[e]];
     }
-  }
-  const double A = (__shfl_sync(0xffffffffu, part, 0, 16) + __shfl_sync(0xffffffffu, part, 1, 16)) +
-                   __shfl_sync(0xffffffffu, part, 2, 16);
-  const double P0 = __shfl_sync(0xffffffffu, part, 4, 16);
-  const double P1 = __shfl_sync(0xffffffffu, part, 5, 16);
-  double v = 0.0;
-  if (pos) {
-    const double xs = p.g.oscale_x[ax];  // the tables hold x / xs
-    if (t == Q_RHO) {
-      v = to_f64(q[0]);
-    } else if (t >= Q_X && t < Q_X + 3) {
-      const int d = t - Q_X;
-      if (d == ax)
-        v = to_f64(q[1]) * xs;
-      else if (d < nd)
-        v = (p.g.xmin[d] + (double)gi[d] * p.g.dx[d]) * to_f64(q[0]);
-    } else if (t >= Q_XX && t < Q_XX + 3) {
-      const int d = t - Q_XX;
-      if (d == ax) {
-        v = to_f64(q[2]) * (xs * xs);
-      } else if (d < nd) {
-        const double x = p.g.xmin[d] + (double)gi[d] * p.g.dx[d];
-        v = x * x * to_f64(q[0]);
-      }
-    } else if (t == Q_V) {
-      v = to_f64(q[3]) + A * to_f64(q[0]);
-      if (p.ngauss > 0) v += P0 * to_f64(q[4]);
-      if (p.ngauss > 1) v += P1 * to_f64(q[5]);
-    } else if (t == Q_AC_RE) {
-      v = to_f64(q[6]);
-    } else if (t == Q_AC_IM) {
-      v = to_f64(q[7]);
+    if (p.ngauss > 1) {
+      P1 = (float)p.ctrl->gcoef[1];
+#pragma unroll
+      for (int e = 0; e < 3; e++)
+        if (e < nd && e != ax) P1 *= p.G[1][e][gi[e]];
     }
+    if (t == Q_RHO)
+      v = lt0;
+    else if (t < Q_V)
+      v = d < nd ? mom : 0.0f;
+    else if (t == Q_V)
+      v = fmaf(P1, q[5], fmaf(P0, q[4], fmaf(A, lt0, q[3])));
+    else if (t == Q_AC_RE)
+      v = q[6];
+    else if (t == Q_AC_IM)
+      v = q[7];
   } else {
-    const double ks = p.g.oscale_k[ax];  // the tables hold k / ks
+    // k_e / oscale_k[e] of the line on the other axes
+    float kr[3];
+#pragma unroll
+    for (int e = 0; e < 3; e++) {
+      const int n = 1 << g.ln[e];
+      kr[e] = (float)(gi[e] < (n >> 1) ? gi[e] : gi[e] - n) * g.kr[e];
+    }
     if (t == Q_RHOK) {
-      v = to_f64(q[0]);
+      v = lt0;
     } else if (t >= Q_K && t < Q_K + 3) {
       const int d = t - Q_K;
-      if (d == ax)
-        v = to_f64(q[1]) * ks;
-      else if (d < nd)
-        v = wavenumber(p.g, d, gi[d]) * to_f64(q[0]);
+      v = d >= nd ? 0.0f : (d == ax ? q[1] : (d == 0 ? kr[0] : (d == 1 ? kr[1] : kr[2])) * lt0);
     } else if (t == Q_K2) {
-      double k2 = 0.0;
-      for (int d = 0; d < nd; d++) {
-        if (d == ax) continue;
-        const double k = wavenumber(p.g, d, gi[d]);
-        k2 += k * k;
-      }
-      v = to_f64(q[2]) * (ks * ks) + k2 * to_f64(q[0]);
+      float k2 = 0.0f;
+#pragma unroll
+      for (int e = 0; e < 3; e++)
+        if (e < nd && e != ax) k2 = fmaf(kr[e] * kr[e], g.k2r[e], k2);
+      v = fmaf(q[2], ax == 0 ? g.k2r[0] : (ax == 1 ? g.k2r[1] : g.k2r[2]), k2 * lt0);
     }
   }
   red[l][t] = v;
   __syncthreads();
   if (threadIdx.x < NQ) {
+    const int s = threadIdx.x;
     double sum = 0.0;
-    for (int k = 0; k < lines_of<T>(); k++) sum += red[k][threadIdx.x];
-    p.partials[blockIdx.x * (int64_t)NQ + threadIdx.x] = sum;
+    for (int k = 0; k < lines_of<T>(); k++) sum += (double)red[k][s];
+    double scale = 1.0;
+    if (pos) {
+      if (s >= Q_X && s < Q_X + 3) scale = g.oscale_x[s - Q_X];
+      if (s >= Q_XX && s < Q_XX + 3) scale = g.oscale_x[s - Q_XX] * g.oscale_x[s - Q_XX];
+    } else {
+      if (s >= Q_K && s < Q_K + 3) scale = g.oscale_k[s - Q_K];
+      if (s == Q_K2) scale = g.k2s;
+    }
+    p.partials[blockIdx.x * (int64_t)NQ + s] = sum * scale;
   }
 }
 
