@@ -325,6 +325,16 @@ const char* wp_server_last_error(const wp_server* s);
  * tflops), WP_ECUDA. */
 wp_status wp_probe_fma_rate(int32_t fp64, void* stream, double* tflops);
 
+/* Accuracy probe of the complex64 tables' phase factors. The paper has no counterpart of
+ * this call. The complex64 form forms exp(-i A tau/hbar) with FP64 only in the reduction
+ * of the argument modulo pi/2 and the cosine and sine as float-float pairs (Taylor series
+ * on the FP32 pipe). This call evaluates that factor on the current device for n
+ * arguments spread evenly over [-amax, amax] and returns in *max_err the largest absolute
+ * difference of its cosine or sine (high + low part, summed in FP64) from the FP64
+ * sincos of the same argument. Runs on `stream` (NULL = legacy default) and synchronises
+ * it. Errors: WP_EINVAL (n < 1, amax not positive and finite, NULL max_err), WP_ECUDA. */
+wp_status wp_probe_phase_ff(int64_t n, double amax, void* stream, double* max_err);
+
 /* Allocation-free moments. The paper has no counterpart of this call: it exists for
  * callers that cannot call cudaMalloc (a host application whose device memory is held
  * by its own pool or reserved up front, code in a callback where allocation is not

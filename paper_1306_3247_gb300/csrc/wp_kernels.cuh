@@ -18,6 +18,7 @@
 
 #include "wp_fft_f64.h"
 #include "wp_ff.cuh"
+#include "wp_phase_ff.cuh"
 #include "wp_internal.h"
 
 namespace wp {
@@ -1367,6 +1368,7 @@ __device__ void prep_body(const PrepParams<T>& p, int blk, int nblk) {
   __shared__ double fco[WP_MAX_TERMS];
   if (threadIdx.x < pot.nterms) fco[threadIdx.x] = term_coef(pot.term[threadIdx.x], t);
   __syncthreads();
+  [[maybe_unused]] const double tau_hbar = p.tau / p.g.hbar;
   // one flat range over the entries of all axes, so that short axes share a round
   const int64_t n01 = p.n[0] + (p.g.ndim > 1 ? p.n[1] : 0);
   const int64_t nall = n01 + (p.g.ndim > 2 ? p.n[2] : 0);
@@ -1385,12 +1387,25 @@ __device__ void prep_body(const PrepParams<T>& p, int blk, int nblk) {
       }
       tb.A[i] = A;
       if (tb.AT) tb.AT[i] = (T)A;
-      double sn, cs;
-      sincos(-A * p.tau / p.g.hbar, &sn, &cs);
-      const T hc = (T)cs, hs = (T)sn;
-      tb.P[i] = mk(hc, hs);
-      tb.P_lo[i] = mk((T)(cs - (double)hc), (T)(sn - (double)hs));
-      tb.Prec[i] = make_rec<T>(cs, sn);
+      if constexpr (std::is_same<T, float>::value) {
+        // complex64: the factor's high and low parts straight from the float-float cos and
+        // sin of the argument (FP64 only reduces it)
+        ff c, sn;
+        cis_ff(-A * tau_hbar, c, sn);
+        TwE<float> r;
+        r.h = mk(c.hi, sn.hi);
+        r.l = mk(c.lo, sn.lo);
+        tb.P[i] = r.h;
+        tb.P_lo[i] = r.l;
+        tb.Prec[i] = r;
+      } else {
+        double sn, cs;
+        sincos(-A * p.tau / p.g.hbar, &sn, &cs);
+        const T hc = (T)cs, hs = (T)sn;
+        tb.P[i] = mk(hc, hs);
+        tb.P_lo[i] = mk((T)(cs - (double)hc), (T)(sn - (double)hs));
+        tb.Prec[i] = make_rec<T>(cs, sn);
+      }
       for (int gg = 0; gg < pot.ngauss; gg++) {
         const double gf = gauss_axis_factor(pot.term[pot.gauss_term[gg]], d, x, t);
         tb.Gd[gg][i] = gf;

@@ -9,11 +9,17 @@
 // values stay bounded), enough warps per SM to cover the pipe latency (8 blocks of 256
 // threads per SM), timed with CUDA events around a second launch (the first warms up).
 // One chain step is one FMA = 2 floating-point operations.
+//
+// The phase-factor accuracy probe evaluates the complex64 tables' float-float cosine and
+// sine (wp_phase_ff.cuh) against the FP64 sincos on a grid of arguments.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "wavepacket_gpu.h"
+#include "wp_phase_ff.cuh"
 
 namespace {
 
@@ -35,9 +41,54 @@ __global__ void __launch_bounds__(256) k_probe_fma(T a, T b, int iters, T* sink)
   if (s == (T)-1) sink[0] = s;
 }
 
+// Largest |cos - cos_ref| or |sin - sin_ref| over arguments amax (2 (i + 1/2)/n - 1),
+// i < n, as the bit pattern of a non-negative double (such patterns order like the values).
+__global__ void __launch_bounds__(256) k_probe_phase_ff(int64_t n, double amax, unsigned long long* worst_bits) {
+  double worst = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double th = amax * (2.0 * ((double)i + 0.5) / (double)n - 1.0);
+    wp::ff c, s;
+    wp::cis_ff(th, c, s);
+    double sd, cd;
+    sincos(th, &sd, &cd);
+    const double e = fmax(fabs(((double)c.hi + (double)c.lo) - cd), fabs(((double)s.hi + (double)s.lo) - sd));
+    worst = fmax(worst, e);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(worst_bits, (unsigned long long)__double_as_longlong(worst));
+}
+
 }  // namespace
 
 extern "C" {
+
+// See include/wavepacket_gpu.h for the contract.
+wp_status wp_probe_phase_ff(int64_t n, double amax, void* stream, double* max_err) {
+  if (!max_err || n < 1 || !(amax > 0.0) || !std::isfinite(amax)) return WP_EINVAL;
+  *max_err = 0.0;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned long long* d = nullptr;
+  (void)cudaGetLastError();
+  if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return WP_ECUDA;
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned long long), st);
+  if (e == cudaSuccess) {
+    const int64_t want = (n + 255) / 256;
+    const unsigned blocks = (unsigned)(want < 4096 ? want : 4096);
+    k_probe_phase_ff<<<blocks, 256, 0, st>>>(n, amax, d);
+    e = cudaGetLastError();
+  }
+  unsigned long long bits = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, d, sizeof(bits), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return WP_ECUDA;
+  double v;
+  static_assert(sizeof(v) == sizeof(bits), "double and its bit pattern");
+  memcpy(&v, &bits, sizeof(v));
+  *max_err = v;
+  return WP_OK;
+}
 
 // See include/wavepacket_gpu.h for the contract.
 wp_status wp_probe_fma_rate(int32_t fp64, void* stream, double* tflops) {
