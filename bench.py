@@ -18,10 +18,10 @@ over all ranks.
              FP64 form on a seeded sample of 256 of the same instances.
   served  -- the seeded Poisson request stream (2000 requests of 1-D/2-D/3-D jobs,
              complex64) through the continuous-batching server under an 80 GB budget:
-             p50/p99 latency, offered and achieved rates; then its first 500 requests
-             offered below the achieved rate.
+             p50/p99 latency, offered and achieved rates; then its first 500 and its
+             first 120 requests offered below the achieved rate.
 
---impl reference times the FP64 CPU oracle (the checker) on a bounded sample of the
+--impl reference times the FP64 CPU oracle on a bounded sample of the
 3-D workload on the host cores. With --gpus N > 1 (torchrun) every rank runs an
 independent replica ("replicas only": the method has no exchange step).
 """
